@@ -1,0 +1,237 @@
+/*
+ * bcgpu.h - weighted betweenness centrality on one GB300 (sm_103a), C ABI.
+ *
+ * Method: arxiv 1701.05975, "A GPU-Based Solution to Fast Calculation of
+ * Betweenness Centrality on Large Weighted Networks".  For every source s in a
+ * caller-given list the library runs Brandes' algorithm (Sec. 2.1): exact
+ * single-source shortest paths over the weighted CSR graph with the strict
+ * settle criterion of Sec. 3.2 (Eq. 2 with Eq. 4), the shortest-path counts
+ * sigma over the resulting DAG, and the backward dependency accumulation
+ * delta (Algorithm 3) summed into per-vertex BC.
+ *
+ * Result convention:  out_bc[v] = scale * sum_{s in sources} delta_s(v),
+ *   delta_s(v) = sum_{t != s, v} sigma_st(v) / sigma_st          (Eq. 1 terms).
+ * With sources = V and scale = 1 this is Eq. 1 over ordered pairs; pass
+ * scale = 0.5 for the usual undirected value, 0.5 * n / k when the k sources
+ * are a uniform sample.  Duplicate sources count twice.
+ *
+ * Graph convention (Sec. 3.1): CSR row_ptr (n + 1 entries, row_ptr[0] = 0,
+ * non-decreasing, row_ptr[n] = nnz), col_idx (nnz entries < n) and a parallel
+ * weight array (nnz entries, each >= 1).  The graph is undirected (Sec. 2.1):
+ * each edge {u, v, w} must be stored as both (u -> v, w) and (v -> u, w).
+ * Every CSR entry is a distinct edge: parallel equal-weight entries each count
+ * as a shortest path; self-loops are allowed and never lie on a shortest path.
+ * A weight of 0 is rejected (the strict criterion of Eq. 4 can stall on it).
+ *
+ * Numbers: distances are exact integers (uint64 on the ABI; the device keeps
+ * uint32 when n * max_weight * 2 < 2^32, else uint64), sigma, delta and BC
+ * are IEEE double.
+ *
+ * Errors: every function returns BC_OK (0) or one of the BC_ERR_* codes
+ * below; no C++ exception crosses the ABI.  bc_last_error() returns a
+ * thread-local message for the last failing call on the calling thread.
+ *
+ * Threads: all functions are thread-safe.  All device work runs on the
+ * current CUDA device of the calling thread at bc_graph_create time.
+ */
+#ifndef BCGPU_H
+#define BCGPU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define BC_OK 0
+#define BC_ERR_INVALID 1   /* malformed CSR, weight 0, source >= n, bad handle or argument */
+#define BC_ERR_NOMEM 2     /* device or host allocation failed, or the request exceeds the memory budget */
+#define BC_ERR_CUDA 3      /* a CUDA runtime call failed (message in bc_last_error) */
+#define BC_ERR_TIMEOUT 4   /* a device loop hit its iteration cap, or a wait timed out */
+#define BC_ERR_BUSY 5      /* the serving queue is full */
+#define BC_ERR_CANCELLED 6 /* the request was cancelled */
+
+/* ---- graph flags ------------------------------------------------------- */
+#define BC_UNDIRECTED_CHECK 0x1u /* verify that every (u -> v, w) entry has a (v -> u, w) twin */
+
+/* ---- execution modes --------------------------------------------------- */
+#define BC_MODE_BATCHED 0u /* persistent launch: one team (warp or CTA) per source, many sources in flight */
+#define BC_MODE_PLAIN 1u   /* one source at a time over the whole GPU, host-driven phase loop */
+
+/* ---- request states (bc_request_poll) ---------------------------------- */
+#define BC_REQ_QUEUED 0
+#define BC_REQ_RUNNING 1
+#define BC_REQ_DONE 2
+#define BC_REQ_FAILED 3
+#define BC_REQ_CANCELLED 4
+
+typedef struct bc_graph *bc_graph_t;
+typedef uint64_t bc_request_t;
+
+/*
+ * Tuning and test knobs (process-wide).  A zero field means "automatic":
+ * the autotuner (bc_autotune) or the built-in defaults choose it.
+ */
+typedef struct bc_config {
+  uint32_t mode;          /* BC_MODE_BATCHED or BC_MODE_PLAIN */
+  uint32_t team_threads;  /* threads that share one source: 32 (warp team) or 128/256/512 (CTA team) */
+  uint32_t max_slots;     /* cap on sources in flight at once (per-source slabs held in device memory) */
+  uint32_t settle_in;     /* 1: settle by the strict OUT criterion (Eq. 2 + Eq. 4) OR the strict IN
+                             criterion; 2: OUT only (the paper's criterion alone); 0 = automatic (1) */
+  uint64_t bucket_width;  /* near/far split width, in distance units (>= 1) */
+  uint64_t phase_cap;     /* device cap on phases per source; hitting it returns BC_ERR_TIMEOUT */
+  double mem_fraction;    /* share of free device memory the slabs may take (0 < f <= 0.95) */
+} bc_config;
+
+/* Read the current process-wide configuration. */
+int bc_get_config(bc_config *out);
+
+/* Replace the process-wide configuration (validated; BC_ERR_INVALID on a bad field). */
+int bc_set_config(const bc_config *cfg);
+
+/* Thread-local description of the last error on this thread ("" if none). */
+const char *bc_last_error(void);
+
+/*
+ * Upload a graph (Sec. 3.1 CSR + weight array) to the current device.
+ * row_ptr[n + 1], col_idx[nnz] and w[nnz] are HOST arrays; the library copies
+ * them and the caller keeps ownership.  Validation: n >= 1, row_ptr[0] = 0,
+ * non-decreasing, row_ptr[n] = nnz, col_idx < n, w >= 1; with
+ * BC_UNDIRECTED_CHECK also the symmetry of the entries.  Precomputes
+ * Delta_node(v) = min incident weight (Sec. 3.2, before Eq. 2).
+ * On success *out holds an opaque handle that bc_graph_destroy releases.
+ */
+int bc_graph_create(const uint64_t *row_ptr, const uint32_t *col_idx, const uint32_t *w, uint32_t n,
+                    uint64_t nnz, uint32_t flags, bc_graph_t *out);
+
+/* Release a graph.  Fails with BC_ERR_BUSY while serving requests still use it. */
+int bc_graph_destroy(bc_graph_t g);
+
+typedef struct bc_graph_info {
+  uint32_t n;
+  uint64_t nnz;
+  uint32_t max_weight;
+  uint32_t dist_bits;     /* 32 or 64: device distance width chosen for this graph */
+  uint64_t device_bytes;  /* resident CSR + per-vertex graph data */
+  uint64_t slab_bytes;    /* device bytes one in-flight source needs */
+} bc_graph_info;
+
+int bc_graph_get_info(bc_graph_t g, bc_graph_info *out);
+
+/*
+ * Synchronous BC over a source list (Sec. 2.1, Algorithms 1-3).
+ * sources[k] and out_bc[n] are HOST arrays owned by the caller; out_bc is
+ * overwritten with scale * sum_s delta_s.  k = 0 yields all zeros.
+ */
+int bc_compute(bc_graph_t g, const uint32_t *sources, uint32_t k, double scale, double *out_bc);
+
+/*
+ * Asynchronous BC on a caller stream.  d_sources[k] and d_out_bc[n] are
+ * DEVICE arrays owned by the caller (e.g. torch tensors); stream is a
+ * cudaStream_t (NULL = legacy default stream).  Returns after enqueueing;
+ * d_out_bc is valid once the stream reaches that point.  Sources are
+ * validated on the device: an out-of-range source sets the graph's error word,
+ * which bc_sync_status() reports as BC_ERR_INVALID.
+ */
+int bc_compute_async(bc_graph_t g, const uint32_t *d_sources, uint32_t k, double scale, double *d_out_bc,
+                     void *stream);
+
+/*
+ * Wait for all work enqueued on `stream` by bc_compute_async for graph g and
+ * return the status recorded by its kernels (BC_OK, BC_ERR_TIMEOUT, BC_ERR_INVALID).
+ */
+int bc_sync_status(bc_graph_t g, void *stream);
+
+/*
+ * Edge betweenness (the paper's tool reports node and edge BC, Sec. 1).
+ * out_ebc[nnz] (HOST) receives, per CSR entry e = (a -> b, w):
+ *   scale * sum_s sigma_sa / sigma_sb * (1 + delta_s(b))   when d(a) + w = d(b),
+ * i.e. the dependency share that crosses the entry from a to b; 0 otherwise.
+ * The undirected edge {a, b} carries the sum of its two entries.  out_bc[n]
+ * (HOST, may be NULL) receives the vertex BC of the same run.
+ */
+int bc_edge_compute(bc_graph_t g, const uint32_t *sources, uint32_t k, double scale, double *out_ebc,
+                    double *out_bc);
+
+/*
+ * Serving (continuous batching).  Submit copies sources[k] at the call; the
+ * HOST array out_bc[n] must stay valid until the request is DONE, FAILED or
+ * CANCELLED.  Requests on different graphs and sizes are admitted as device
+ * memory and source slots free up and run concurrently on separate streams.
+ * BC_ERR_NOMEM: the request alone can never fit the memory budget.
+ * BC_ERR_BUSY: the pending queue is full.
+ */
+int bc_request_submit(bc_graph_t g, const uint32_t *sources, uint32_t k, double scale, double *out_bc,
+                      bc_request_t *out_id);
+
+/* Current state of a request (BC_REQ_*); BC_ERR_INVALID for an unknown id. */
+int bc_request_poll(bc_request_t id, int *out_state);
+
+/*
+ * Block until the request leaves QUEUED/RUNNING or timeout_ms passes
+ * (timeout_ms < 0: no limit).  Returns BC_OK when DONE, the request's error
+ * code when FAILED, BC_ERR_CANCELLED when cancelled, BC_ERR_TIMEOUT on timeout.
+ * A request that has finished is forgotten after bc_request_wait returns.
+ */
+int bc_request_wait(bc_request_t id, int timeout_ms);
+
+/* Cancel a QUEUED request (BC_OK) ; a RUNNING one finishes (BC_ERR_BUSY). */
+int bc_request_cancel(bc_request_t id);
+
+/* Serving statistics: requests completed and their latencies (submit -> done). */
+typedef struct bc_serving_stats {
+  uint64_t completed;
+  uint64_t failed;
+  double p50_ms;
+  double p99_ms;
+  double mean_ms;
+  uint64_t edges_traversed; /* sum over completed requests of k * (nnz / 2) */
+  uint32_t max_concurrent;  /* largest number of requests seen running at once */
+} bc_serving_stats;
+
+int bc_serving_stats_get(bc_serving_stats *out);
+int bc_serving_reset(void);
+
+/*
+ * Test hook: distances (UINT64_MAX = unreachable), shortest-path counts and
+ * the settle batch (level) of every vertex from one source, as the batched
+ * path computes them (Algorithm 2 semantics, strict criterion).  HOST outputs
+ * of n entries each; any may be NULL.  Unreached vertices get level
+ * UINT32_MAX.  Within a source, every shortest-path DAG edge (p -> v)
+ * satisfies level[p] < level[v].
+ */
+int bc_sssp_debug(bc_graph_t g, uint32_t s, uint64_t *out_dist, double *out_sigma, uint32_t *out_level);
+
+/*
+ * Per-run counters of the last batched run on this thread's last-used graph:
+ * phases (settle batches) summed over sources, near/far refills, levels,
+ * relaxations attempted (atomicMin issued) and reached vertices.
+ */
+typedef struct bc_run_stats {
+  uint64_t sources;
+  uint64_t phases;
+  uint64_t refills;
+  uint64_t reached;
+  uint64_t relax_atomics;
+  uint64_t entries_scanned;
+  uint32_t team_threads;
+  uint32_t slots;
+  uint64_t bucket_width;
+} bc_run_stats;
+
+int bc_last_run_stats(bc_graph_t g, bc_run_stats *out);
+
+/*
+ * Autotuner: times candidate (team size, bucket width, settle rule) settings
+ * on a probe sample of `sources` (k_probe of them, HOST array) and stores the
+ * fastest as the graph's tuned configuration, used whenever the process-wide
+ * config leaves a field at 0.  Results are cached per graph fingerprint.
+ */
+int bc_autotune(bc_graph_t g, const uint32_t *sources, uint32_t k_probe);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BCGPU_H */

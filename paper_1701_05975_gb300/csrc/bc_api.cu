@@ -1,0 +1,754 @@
+// C-ABI of libbcgpu (declared in include/bcgpu.h): graph residency, per-source
+// slab workspaces, the batched and plain execution paths, the test hook, the
+// autotuner and the continuous-batching request server.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/bcgpu.h"
+#include "bc_common.h"
+
+using namespace bcgpu;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return fail(BC_ERR_NOMEM, "%s: %s", where, cudaGetErrorString(e));
+  }
+  return fail(BC_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CK(call)                                         \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+  } while (0)
+
+std::mutex g_cfg_mu;
+bc_config g_cfg = {BC_MODE_BATCHED, 0, 0, 0, 0, 0, 0.0};
+
+bc_config config_snapshot() {
+  std::lock_guard<std::mutex> lk(g_cfg_mu);
+  return g_cfg;
+}
+
+uint64_t align256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
+
+SlabLayout make_layout(uint32_t n, int dist_bits) {
+  SlabLayout L{};
+  uint64_t off = 0;
+  L.off_d = off;
+  off += align256((uint64_t)n * (dist_bits / 8));
+  L.off_sig = off;
+  off += align256((uint64_t)n * 8);
+  L.off_S = off;
+  off += align256((uint64_t)n * 4);
+  L.off_ends = off;
+  off += align256(((uint64_t)n + 2) * 4);
+  L.off_near = off;
+  off += align256((uint64_t)n * 4);
+  L.off_far = off;
+  off += align256((uint64_t)n * 4);
+  L.stride = off;
+  return L;
+}
+
+// Control block of one launch: source counter, status word, counters, debug.
+struct Ctl {
+  uint32_t counter;
+  int err;
+  uint32_t debug[2];
+  unsigned long long stats[STAT_COUNT];
+};
+
+// Device memory for `slots` sources in flight plus per-call buffers.
+struct Workspace {
+  uint32_t slots = 0;
+  SlabLayout lay{};
+  char* slabs = nullptr;
+  Ctl* ctl = nullptr;
+  double* bc = nullptr;      // [n] (sync paths)
+  uint32_t* src = nullptr;   // device copy of the source list
+  uint32_t src_cap = 0;
+  Ctl* host_ctl = nullptr;   // pinned
+  uint32_t* host_src = nullptr;  // pinned staging for sources
+  double* host_bc = nullptr;     // pinned staging for results
+  cudaEvent_t done = nullptr;
+  bool busy = false;
+  uint64_t bytes = 0;
+};
+
+struct TuneCfg {
+  uint32_t team = 0;
+  uint64_t width = 0;
+  uint32_t settle_in = 0;
+};
+
+std::mutex g_tune_mu;
+std::map<std::string, TuneCfg> g_tune_cache;  // fingerprint -> tuned settings
+
+}  // namespace
+
+struct bc_graph {
+  int device = 0;
+  uint32_t n = 0;
+  uint64_t nnz = 0;
+  uint32_t max_w = 0;
+  int dist_bits = 64;
+  int sm_count = 0;
+  uint64_t* row_ptr = nullptr;
+  uint2* adj = nullptr;
+  uint32_t* dnode = nullptr;
+  double* ebc = nullptr;  // lazily allocated [nnz]
+  uint64_t device_bytes = 0;
+  std::string fingerprint;
+  TuneCfg tuned;
+  std::mutex mu;  // guards the workspace pool and stats
+  std::vector<std::unique_ptr<Workspace>> pool;
+  std::unordered_map<cudaStream_t, Workspace*> async_ws;
+  bc_run_stats last{};
+  std::atomic<int> serving_refs{0};
+  PlainWork* plain = nullptr;
+  cudaStream_t stream = nullptr;  // internal stream of the synchronous calls
+};
+
+namespace {
+
+GraphDev view(const bc_graph* g) {
+  GraphDev v;
+  v.n = g->n;
+  v.nnz = g->nnz;
+  v.row_ptr = g->row_ptr;
+  v.adj = g->adj;
+  v.dnode = g->dnode;
+  return v;
+}
+
+void ws_free(Workspace* w) {
+  if (!w) return;
+  cudaFree(w->slabs);
+  cudaFree(w->ctl);
+  cudaFree(w->bc);
+  cudaFree(w->src);
+  if (w->host_ctl) cudaFreeHost(w->host_ctl);
+  if (w->host_src) cudaFreeHost(w->host_src);
+  if (w->host_bc) cudaFreeHost(w->host_bc);
+  if (w->done) cudaEventDestroy(w->done);
+}
+
+// Settings for a run: explicit config fields win, then the graph's tuned
+// values, then heuristics.
+struct RunCfg {
+  uint32_t team;
+  uint64_t width;
+  uint32_t settle_in;
+  uint64_t phase_cap;
+  uint32_t max_slots;
+  double mem_fraction;
+  uint32_t mode;
+};
+
+RunCfg resolve(const bc_graph* g) {
+  bc_config c = config_snapshot();
+  RunCfg r;
+  r.mode = c.mode;
+  const double avg_deg = g->n ? (double)g->nnz / g->n : 0.0;
+  r.team = c.team_threads ? c.team_threads
+                          : (g->tuned.team ? g->tuned.team : ((avg_deg <= 12.0 || g->n <= 8192) ? 32u : 256u));
+  r.width = c.bucket_width ? c.bucket_width
+                           : (g->tuned.width ? g->tuned.width : std::max<uint64_t>(1, g->max_w / 4));
+  uint32_t si = c.settle_in ? c.settle_in : (g->tuned.settle_in ? g->tuned.settle_in : 1u);
+  r.settle_in = (si == 1u) ? 1u : 0u;
+  r.phase_cap = c.phase_cap ? c.phase_cap : 2ull * g->n + 64;
+  r.max_slots = c.max_slots;
+  r.mem_fraction = c.mem_fraction > 0 ? c.mem_fraction : 0.6;
+  return r;
+}
+
+// Number of sources in flight for a run of k sources.
+int plan_slots(const bc_graph* g, const RunCfg& r, uint32_t k, uint32_t* slots_out) {
+  int bps = 0;
+  cudaError_t e = batched_occupancy(g->dist_bits, (int)r.team, &bps);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+  const uint32_t per_block = (uint32_t)(batched_block_threads((int)r.team) / (int)r.team);
+  uint64_t slots = (uint64_t)std::max(bps, 1) * g->sm_count * per_block;
+  size_t free_b = 0, total_b = 0;
+  CK(cudaMemGetInfo(&free_b, &total_b));
+  const uint64_t stride = make_layout(g->n, g->dist_bits).stride;
+  const uint64_t by_mem = (uint64_t)((double)free_b * r.mem_fraction) / std::max<uint64_t>(stride, 1);
+  slots = std::min<uint64_t>(slots, by_mem);
+  if (r.max_slots) slots = std::min<uint64_t>(slots, r.max_slots);
+  slots = std::min<uint64_t>(slots, std::max<uint32_t>(k, 1));
+  if (slots == 0) return fail(BC_ERR_NOMEM, "device memory too small for one per-source slab (%llu bytes)",
+                              (unsigned long long)stride);
+  *slots_out = (uint32_t)slots;
+  return BC_OK;
+}
+
+// Acquire a free workspace with >= slots slabs and a source buffer >= k.
+// The caller's stream waits for the workspace's previous use.
+int ws_acquire(bc_graph* g, uint32_t slots, uint32_t k, cudaStream_t st, Workspace** out) {
+  Workspace* w = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g->mu);
+    for (auto& p : g->pool)
+      if (!p->busy && p->slots >= slots && (!w || p->slots < w->slots)) w = p.get();
+    if (w) w->busy = true;
+  }
+  if (!w) {
+    auto nw = std::make_unique<Workspace>();
+    nw->slots = slots;
+    nw->lay = make_layout(g->n, g->dist_bits);
+    const uint64_t bytes = nw->lay.stride * slots;
+    cudaError_t e = cudaMalloc(&nw->slabs, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&nw->ctl, sizeof(Ctl));
+    if (e == cudaSuccess) e = cudaMalloc(&nw->bc, (size_t)g->n * 8);
+    if (e == cudaSuccess) e = cudaMallocHost(&nw->host_ctl, sizeof(Ctl));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&nw->done, cudaEventDisableTiming);
+    // the slab invariant: every distance word is INF between sources
+    // (all-ones bytes everywhere: the other arrays are written before read)
+    if (e == cudaSuccess) e = cudaMemsetAsync(nw->slabs, 0xff, bytes, st);
+    if (e != cudaSuccess) {
+      ws_free(nw.get());
+      return cuda_fail(e, "workspace allocation");
+    }
+    nw->bytes = bytes;
+    nw->busy = true;
+    w = nw.get();
+    std::lock_guard<std::mutex> lk(g->mu);
+    g->pool.push_back(std::move(nw));
+  } else {
+    CK(cudaStreamWaitEvent(st, w->done, 0));
+  }
+  if (w->src_cap < k) {
+    // previous uses of this workspace are ordered before st; free is safe after a sync
+    if (w->src) {
+      CK(cudaStreamSynchronize(st));
+      cudaFree(w->src);
+      cudaFreeHost(w->host_src);
+      w->src = nullptr;
+      w->host_src = nullptr;
+    }
+    const uint32_t cap = std::max<uint32_t>(k, 1024);
+    CK(cudaMalloc(&w->src, (size_t)cap * 4));
+    CK(cudaMallocHost(&w->host_src, (size_t)cap * 4));
+    w->src_cap = cap;
+  }
+  *out = w;
+  return BC_OK;
+}
+
+void ws_release(bc_graph* g, Workspace* w, cudaStream_t st) {
+  cudaEventRecord(w->done, st);
+  std::lock_guard<std::mutex> lk(g->mu);
+  w->busy = false;
+}
+
+BatchArgs make_args(bc_graph* g, Workspace* w, const RunCfg& r, const uint32_t* d_src, uint32_t k, double* d_bc,
+                    double* d_ebc, uint32_t slots, uint32_t flags) {
+  BatchArgs a{};
+  a.g = view(g);
+  a.sources = d_src;
+  a.k = k;
+  a.counter = &w->ctl->counter;
+  a.bc = d_bc;
+  a.ebc = d_ebc;
+  a.slabs = w->slabs;
+  a.lay = w->lay;
+  a.nslots = slots;
+  a.width = r.width;
+  a.settle_in = r.settle_in;
+  a.phase_cap = r.phase_cap;
+  a.err = &w->ctl->err;
+  a.stats = w->ctl->stats;
+  a.flags = flags;
+  a.debug_out = w->ctl->debug;
+  return a;
+}
+
+int grid_for_slots(uint32_t team, uint32_t slots) {
+  const uint32_t per_block = (uint32_t)(batched_block_threads((int)team) / (int)team);
+  return (int)((slots + per_block - 1) / per_block);
+}
+
+// Enqueue one batched run: zero the output and control block, launch, scale.
+int enqueue_batched(bc_graph* g, Workspace* w, const RunCfg& r, const uint32_t* d_src, uint32_t k, double scale,
+                    double* d_bc, double* d_ebc, uint32_t slots, uint32_t flags, cudaStream_t st, bool check_src) {
+  CK(cudaMemsetAsync(w->ctl, 0, sizeof(Ctl), st));
+  if (d_bc) CK(cudaMemsetAsync(d_bc, 0, (size_t)g->n * 8, st));
+  if (d_ebc) CK(cudaMemsetAsync(d_ebc, 0, (size_t)g->nnz * 8, st));
+  if (check_src) CK(launch_check_sources(d_src, k, g->n, &w->ctl->err, st));
+  BatchArgs a = make_args(g, w, r, d_src, k, d_bc, d_ebc, slots, flags);
+  CK(launch_batched(a, g->dist_bits, (int)r.team, grid_for_slots(r.team, slots), st));
+  if (d_bc && scale != 1.0) CK(launch_scale(d_bc, g->n, scale, st));
+  if (d_ebc && scale != 1.0) CK(launch_scale(d_ebc, g->nnz, scale, st));
+  return BC_OK;
+}
+
+int status_from_dev(int dev) {
+  if (dev == DEV_OK) return BC_OK;
+  if (dev == DEV_ERR_TIMEOUT) return fail(BC_ERR_TIMEOUT, "device phase cap reached (BC_ERR_TIMEOUT)");
+  if (dev == DEV_ERR_INVALID) return fail(BC_ERR_INVALID, "a source is out of range");
+  return fail(BC_ERR_CUDA, "unknown device status %d", dev);
+}
+
+void record_stats(bc_graph* g, const Ctl& c, const RunCfg& r, uint32_t slots) {
+  std::lock_guard<std::mutex> lk(g->mu);
+  g->last.sources = c.stats[STAT_SOURCES];
+  g->last.phases = c.stats[STAT_PHASES];
+  g->last.refills = c.stats[STAT_REFILLS];
+  g->last.reached = c.stats[STAT_REACHED];
+  g->last.relax_atomics = c.stats[STAT_RELAX];
+  g->last.entries_scanned = c.stats[STAT_ENTRIES];
+  g->last.team_threads = r.team;
+  g->last.slots = slots;
+  g->last.bucket_width = r.width;
+}
+
+int check_graph(bc_graph_t g) {
+  if (!g) return fail(BC_ERR_INVALID, "null graph handle");
+  return BC_OK;
+}
+
+// Synchronous batched run with host sources and host outputs.
+int compute_sync(bc_graph* g, const uint32_t* sources, uint32_t k, double scale, double* out_bc, double* out_ebc,
+                 const RunCfg& r) {
+  for (uint32_t i = 0; i < k; ++i)
+    if (sources[i] >= g->n) return fail(BC_ERR_INVALID, "source %u out of range (n = %u)", sources[i], g->n);
+  cudaStream_t st = g->stream;
+  uint32_t slots = 0;
+  int rc = plan_slots(g, r, k, &slots);
+  if (rc) return rc;
+  Workspace* w = nullptr;
+  if ((rc = ws_acquire(g, slots, k, st, &w))) return rc;
+  if (k) {
+    memcpy(w->host_src, sources, (size_t)k * 4);
+    cudaError_t e = cudaMemcpyAsync(w->src, w->host_src, (size_t)k * 4, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+      ws_release(g, w, st);
+      return cuda_fail(e, "cudaMemcpyAsync(sources)");
+    }
+  }
+  double* d_ebc = nullptr;
+  if (out_ebc) {
+    if (!g->ebc) {
+      cudaError_t e = cudaMalloc(&g->ebc, (size_t)std::max<uint64_t>(g->nnz, 1) * 8);
+      if (e != cudaSuccess) {
+        ws_release(g, w, st);
+        return cuda_fail(e, "cudaMalloc(edge bc)");
+      }
+    }
+    d_ebc = g->ebc;
+  }
+  rc = enqueue_batched(g, w, r, w->src, k, scale, w->bc, d_ebc, slots, 0, st, false);
+  if (rc) {
+    ws_release(g, w, st);
+    return rc;
+  }
+  cudaError_t e = cudaMemcpyAsync(w->host_ctl, w->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && out_bc) e = cudaMemcpyAsync(out_bc, w->bc, (size_t)g->n * 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && out_ebc && g->nnz)
+    e = cudaMemcpyAsync(out_ebc, d_ebc, (size_t)g->nnz * 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  ws_release(g, w, st);
+  if (e != cudaSuccess) return cuda_fail(e, "batched run");
+  record_stats(g, *w->host_ctl, r, slots);
+  return status_from_dev(w->host_ctl->err);
+}
+
+int compute_plain(bc_graph* g, const uint32_t* sources, uint32_t k, double scale, double* out_bc, const RunCfg& r) {
+  for (uint32_t i = 0; i < k; ++i)
+    if (sources[i] >= g->n) return fail(BC_ERR_INVALID, "source %u out of range (n = %u)", sources[i], g->n);
+  cudaStream_t st = g->stream;
+  if (!g->plain) {
+    cudaError_t e;
+    g->plain = plain_create(g->n, g->dist_bits, &e);
+    if (!g->plain) return cuda_fail(e, "plain workspace");
+  }
+  double* d_bc = nullptr;
+  CK(cudaMalloc(&d_bc, (size_t)g->n * 8));
+  cudaError_t e = cudaMemsetAsync(d_bc, 0, (size_t)g->n * 8, st);
+  int dev = DEV_OK;
+  unsigned long long stats[STAT_COUNT] = {0};
+  if (e == cudaSuccess)
+    e = plain_run(g->plain, view(g), g->dist_bits, sources, k, d_bc, r.width, r.settle_in, r.phase_cap, g->sm_count,
+                  st, &dev, stats);
+  if (e == cudaSuccess && scale != 1.0) e = launch_scale(d_bc, g->n, scale, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out_bc, d_bc, (size_t)g->n * 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d_bc);
+  if (e != cudaSuccess) return cuda_fail(e, "plain run");
+  Ctl c{};
+  memcpy(c.stats, stats, sizeof stats);
+  record_stats(g, c, r, 1);
+  return status_from_dev(dev);
+}
+
+std::string fingerprint(uint32_t n, uint64_t nnz, const uint64_t* rp, const uint32_t* col, const uint32_t* w) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](uint64_t x) {
+    h ^= x;
+    h *= 1099511628211ull;
+  };
+  mix(n);
+  mix(nnz);
+  const uint64_t step = std::max<uint64_t>(1, nnz / 4096);
+  for (uint64_t e = 0; e < nnz; e += step) {
+    mix(col[e]);
+    mix(w[e]);
+  }
+  const uint64_t vstep = std::max<uint64_t>(1, n / 4096);
+  for (uint64_t v = 0; v <= n; v += vstep) mix(rp[v]);
+  char buf[64];
+  snprintf(buf, sizeof buf, "%u-%llu-%016llx", n, (unsigned long long)nnz, (unsigned long long)h);
+  return buf;
+}
+
+}  // namespace
+
+// ===================================================================== ABI
+
+extern "C" {
+
+const char* bc_last_error(void) { return g_last_error.c_str(); }
+
+int bc_get_config(bc_config* out) {
+  if (!out) return fail(BC_ERR_INVALID, "null config");
+  *out = config_snapshot();
+  return BC_OK;
+}
+
+int bc_set_config(const bc_config* cfg) {
+  if (!cfg) return fail(BC_ERR_INVALID, "null config");
+  if (cfg->mode != BC_MODE_BATCHED && cfg->mode != BC_MODE_PLAIN) return fail(BC_ERR_INVALID, "bad mode");
+  if (cfg->team_threads && cfg->team_threads != 32 && cfg->team_threads != 128 && cfg->team_threads != 256 &&
+      cfg->team_threads != 512)
+    return fail(BC_ERR_INVALID, "team_threads must be 0, 32, 128, 256 or 512");
+  if (cfg->settle_in > 2) return fail(BC_ERR_INVALID, "settle_in must be 0, 1 or 2");
+  if (cfg->mem_fraction < 0 || cfg->mem_fraction > 0.95) return fail(BC_ERR_INVALID, "mem_fraction out of range");
+  std::lock_guard<std::mutex> lk(g_cfg_mu);
+  g_cfg = *cfg;
+  return BC_OK;
+}
+
+int bc_graph_create(const uint64_t* row_ptr, const uint32_t* col_idx, const uint32_t* w, uint32_t n, uint64_t nnz,
+                    uint32_t flags, bc_graph_t* out) {
+  if (!out) return fail(BC_ERR_INVALID, "null output handle");
+  *out = nullptr;
+  if (n == 0) return fail(BC_ERR_INVALID, "n must be >= 1");
+  if (n > 0xfffffff0u) return fail(BC_ERR_INVALID, "n too large");
+  if (!row_ptr) return fail(BC_ERR_INVALID, "null row_ptr");
+  if (nnz >= (1ull << 32)) return fail(BC_ERR_INVALID, "graphs with 2^32 or more CSR entries are not supported");
+  if (nnz > 0 && (!col_idx || !w)) return fail(BC_ERR_INVALID, "null col_idx or weights");
+  if (row_ptr[0] != 0) return fail(BC_ERR_INVALID, "row_ptr[0] != 0");
+  for (uint32_t v = 0; v < n; ++v)
+    if (row_ptr[v + 1] < row_ptr[v]) return fail(BC_ERR_INVALID, "row_ptr decreases at %u", v);
+  if (row_ptr[n] != nnz) return fail(BC_ERR_INVALID, "row_ptr[n] != nnz");
+  uint32_t max_w = 0;
+  for (uint64_t e = 0; e < nnz; ++e) {
+    if (col_idx[e] >= n) return fail(BC_ERR_INVALID, "col_idx[%llu] = %u out of range", (unsigned long long)e, col_idx[e]);
+    if (w[e] == 0) return fail(BC_ERR_INVALID, "weight 0 at entry %llu", (unsigned long long)e);
+    max_w = std::max(max_w, w[e]);
+  }
+  if (flags & BC_UNDIRECTED_CHECK) {
+    std::vector<std::array<uint32_t, 3>> a, b;
+    a.reserve(nnz);
+    b.reserve(nnz);
+    for (uint32_t v = 0; v < n; ++v)
+      for (uint64_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+        a.push_back({v, col_idx[e], w[e]});
+        b.push_back({col_idx[e], v, w[e]});
+      }
+    std::sort(a.begin(), a.end());
+    std::sort(b.begin(), b.end());
+    if (a != b) return fail(BC_ERR_INVALID, "graph is not symmetric (BC_UNDIRECTED_CHECK)");
+  }
+  auto g = std::make_unique<bc_graph>();
+  CK(cudaGetDevice(&g->device));
+  CK(cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, g->device));
+  g->n = n;
+  g->nnz = nnz;
+  g->max_w = max_w;
+  g->dist_bits = ((uint64_t)n * std::max<uint32_t>(max_w, 1) * 2ull < 0xffffffffull) ? 32 : 64;
+  g->fingerprint = fingerprint(n, nnz, row_ptr, col_idx, w);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(g->fingerprint);
+    if (it != g_tune_cache.end()) g->tuned = it->second;
+  }
+  uint32_t* d_col = nullptr;
+  uint32_t* d_w = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMalloc(&g->row_ptr, ((size_t)n + 1) * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&g->adj, std::max<size_t>(nnz, 1) * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&g->dnode, (size_t)n * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&d_col, std::max<size_t>(nnz, 1) * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&d_w, std::max<size_t>(nnz, 1) * 4);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(g->row_ptr, row_ptr, ((size_t)n + 1) * 8, cudaMemcpyHostToDevice, g->stream);
+  if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(d_col, col_idx, nnz * 4, cudaMemcpyHostToDevice, g->stream);
+  if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(d_w, w, nnz * 4, cudaMemcpyHostToDevice, g->stream);
+  if (e == cudaSuccess) e = launch_prep(n, nnz, g->row_ptr, d_col, d_w, g->adj, g->dnode, g->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+  cudaFree(d_col);
+  cudaFree(d_w);
+  if (e != cudaSuccess) {
+    cudaFree(g->row_ptr);
+    cudaFree(g->adj);
+    cudaFree(g->dnode);
+    if (g->stream) cudaStreamDestroy(g->stream);
+    return cuda_fail(e, "bc_graph_create upload");
+  }
+  g->device_bytes = ((uint64_t)n + 1) * 8 + nnz * 8 + (uint64_t)n * 4;
+  *out = g.release();
+  return BC_OK;
+}
+
+int bc_graph_destroy(bc_graph_t g) {
+  if (int rc = check_graph(g)) return rc;
+  if (g->serving_refs.load() > 0) return fail(BC_ERR_BUSY, "graph still has serving requests");
+  cudaSetDevice(g->device);
+  cudaStreamSynchronize(g->stream);
+  for (auto& w : g->pool) {
+    if (w->done) cudaEventSynchronize(w->done);
+    ws_free(w.get());
+  }
+  g->pool.clear();
+  plain_destroy(g->plain);
+  cudaFree(g->row_ptr);
+  cudaFree(g->adj);
+  cudaFree(g->dnode);
+  cudaFree(g->ebc);
+  cudaStreamDestroy(g->stream);
+  delete g;
+  return BC_OK;
+}
+
+int bc_graph_get_info(bc_graph_t g, bc_graph_info* out) {
+  if (int rc = check_graph(g)) return rc;
+  if (!out) return fail(BC_ERR_INVALID, "null output");
+  out->n = g->n;
+  out->nnz = g->nnz;
+  out->max_weight = g->max_w;
+  out->dist_bits = (uint32_t)g->dist_bits;
+  out->device_bytes = g->device_bytes;
+  out->slab_bytes = make_layout(g->n, g->dist_bits).stride;
+  return BC_OK;
+}
+
+int bc_compute(bc_graph_t g, const uint32_t* sources, uint32_t k, double scale, double* out_bc) {
+  if (int rc = check_graph(g)) return rc;
+  if (!out_bc) return fail(BC_ERR_INVALID, "null out_bc");
+  if (k && !sources) return fail(BC_ERR_INVALID, "null sources");
+  CK(cudaSetDevice(g->device));
+  RunCfg r = resolve(g);
+  if (r.mode == BC_MODE_PLAIN) return compute_plain(g, sources, k, scale, out_bc, r);
+  return compute_sync(g, sources, k, scale, out_bc, nullptr, r);
+}
+
+int bc_compute_async(bc_graph_t g, const uint32_t* d_sources, uint32_t k, double scale, double* d_out_bc,
+                     void* stream) {
+  if (int rc = check_graph(g)) return rc;
+  if (!d_out_bc) return fail(BC_ERR_INVALID, "null d_out_bc");
+  if (k && !d_sources) return fail(BC_ERR_INVALID, "null d_sources");
+  CK(cudaSetDevice(g->device));
+  RunCfg r = resolve(g);
+  if (r.mode != BC_MODE_BATCHED) return fail(BC_ERR_INVALID, "bc_compute_async runs the batched mode only");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint32_t slots = 0;
+  int rc = plan_slots(g, r, k, &slots);
+  if (rc) return rc;
+  Workspace* w = nullptr;
+  if ((rc = ws_acquire(g, slots, 0, st, &w))) return rc;
+  rc = enqueue_batched(g, w, r, d_sources, k, scale, d_out_bc, nullptr, slots, 0, st, true);
+  if (!rc) {
+    cudaError_t e = cudaMemcpyAsync(w->host_ctl, w->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemcpyAsync(control)");
+  }
+  {
+    std::lock_guard<std::mutex> lk(g->mu);
+    g->async_ws[st] = w;
+    g->last.team_threads = r.team;
+    g->last.slots = slots;
+    g->last.bucket_width = r.width;
+  }
+  ws_release(g, w, st);
+  return rc;
+}
+
+int bc_sync_status(bc_graph_t g, void* stream) {
+  if (int rc = check_graph(g)) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CK(cudaSetDevice(g->device));
+  CK(cudaStreamSynchronize(st));
+  Workspace* w = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g->mu);
+    auto it = g->async_ws.find(st);
+    if (it != g->async_ws.end()) w = it->second;
+  }
+  if (!w) return BC_OK;
+  return status_from_dev(w->host_ctl->err);
+}
+
+int bc_edge_compute(bc_graph_t g, const uint32_t* sources, uint32_t k, double scale, double* out_ebc,
+                    double* out_bc) {
+  if (int rc = check_graph(g)) return rc;
+  if (!out_ebc) return fail(BC_ERR_INVALID, "null out_ebc");
+  if (k && !sources) return fail(BC_ERR_INVALID, "null sources");
+  CK(cudaSetDevice(g->device));
+  RunCfg r = resolve(g);
+  std::vector<double> tmp;
+  if (!out_bc) {
+    tmp.resize(g->n);
+    out_bc = tmp.data();
+  }
+  return compute_sync(g, sources, k, scale, out_bc, out_ebc, r);
+}
+
+int bc_sssp_debug(bc_graph_t g, uint32_t s, uint64_t* out_dist, double* out_sigma, uint32_t* out_level) {
+  if (int rc = check_graph(g)) return rc;
+  if (s >= g->n) return fail(BC_ERR_INVALID, "source out of range");
+  CK(cudaSetDevice(g->device));
+  RunCfg r = resolve(g);
+  cudaStream_t st = g->stream;
+  Workspace* w = nullptr;
+  int rc = ws_acquire(g, 1, 1, st, &w);
+  if (rc) return rc;
+  w->host_src[0] = s;
+  const uint32_t n = g->n;
+  std::vector<uint8_t> dbuf((size_t)n * (g->dist_bits / 8));
+  std::vector<double> sig(n);
+  std::vector<uint32_t> S(n), ends((size_t)n + 2);
+  cudaError_t e = cudaMemcpyAsync(w->src, w->host_src, 4, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) {
+    ws_release(g, w, st);
+    return cuda_fail(e, "cudaMemcpyAsync");
+  }
+  rc = enqueue_batched(g, w, r, w->src, 1, 1.0, nullptr, nullptr, 1, RUN_FORWARD_ONLY, st, false);
+  if (rc) {
+    ws_release(g, w, st);
+    return rc;
+  }
+  char* base = w->slabs;
+  e = cudaMemcpyAsync(w->host_ctl, w->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dbuf.data(), base + w->lay.off_d, dbuf.size(), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sig.data(), base + w->lay.off_sig, (size_t)n * 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(S.data(), base + w->lay.off_S, (size_t)n * 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ends.data(), base + w->lay.off_ends, ((size_t)n + 2) * 4, cudaMemcpyDeviceToHost, st);
+  // restore the slab invariant (forward-only runs leave distances behind)
+  if (e == cudaSuccess) e = cudaMemsetAsync(base + w->lay.off_d, 0xff, dbuf.size(), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  ws_release(g, w, st);
+  if (e != cudaSuccess) return cuda_fail(e, "bc_sssp_debug");
+  if ((rc = status_from_dev(w->host_ctl->err))) return rc;
+  const uint32_t nlev = w->host_ctl->debug[0];
+  const uint32_t reached = w->host_ctl->debug[1];
+  std::vector<uint32_t> level(n, 0xffffffffu);
+  for (uint32_t l = 0; l < nlev; ++l)
+    for (uint32_t i = ends[l]; i < ends[l + 1] && i < reached; ++i) level[S[i]] = l;
+  for (uint32_t v = 0; v < n; ++v) {
+    const bool reached_v = level[v] != 0xffffffffu;
+    if (out_dist) {
+      if (!reached_v) out_dist[v] = UINT64_MAX;
+      else if (g->dist_bits == 32) out_dist[v] = reinterpret_cast<const uint32_t*>(dbuf.data())[v];
+      else out_dist[v] = reinterpret_cast<const uint64_t*>(dbuf.data())[v];
+    }
+    if (out_sigma) out_sigma[v] = reached_v ? sig[v] : 0.0;
+    if (out_level) out_level[v] = level[v];
+  }
+  return BC_OK;
+}
+
+int bc_last_run_stats(bc_graph_t g, bc_run_stats* out) {
+  if (int rc = check_graph(g)) return rc;
+  if (!out) return fail(BC_ERR_INVALID, "null output");
+  std::lock_guard<std::mutex> lk(g->mu);
+  *out = g->last;
+  return BC_OK;
+}
+
+int bc_autotune(bc_graph_t g, const uint32_t* sources, uint32_t k_probe) {
+  if (int rc = check_graph(g)) return rc;
+  if (!sources || k_probe == 0) return fail(BC_ERR_INVALID, "autotune needs probe sources");
+  CK(cudaSetDevice(g->device));
+  bc_config user = config_snapshot();
+  const uint32_t teams[] = {32, 128, 256, 512};
+  std::vector<uint64_t> widths;
+  for (uint64_t d : {16ull, 4ull, 1ull}) widths.push_back(std::max<uint64_t>(1, g->max_w / d));
+  widths.push_back(4ull * std::max<uint32_t>(g->max_w, 1));
+  std::vector<double> out(g->n);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best_ms = 1e30f;
+  TuneCfg best;
+  for (uint32_t team : teams) {
+    if (user.team_threads && user.team_threads != team) continue;
+    for (uint64_t width : widths) {
+      if (user.bucket_width && user.bucket_width != width) continue;
+      RunCfg r = resolve(g);
+      r.team = team;
+      r.width = width;
+      r.settle_in = 1;
+      r.mode = BC_MODE_BATCHED;
+      // warm once, then time
+      float ms = 0;
+      for (int rep = 0; rep < 2; ++rep) {
+        cudaEventRecord(e0, g->stream);
+        int rc = compute_sync(g, sources, k_probe, 1.0, out.data(), nullptr, r);
+        cudaEventRecord(e1, g->stream);
+        cudaEventSynchronize(e1);
+        if (rc) {
+          cudaEventDestroy(e0);
+          cudaEventDestroy(e1);
+          return rc;
+        }
+        cudaEventElapsedTime(&ms, e0, e1);
+      }
+      if (ms < best_ms) {
+        best_ms = ms;
+        best.team = team;
+        best.width = width;
+        best.settle_in = 1;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  g->tuned = best;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[g->fingerprint] = best;
+  return BC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,539 @@
+// Batched Brandes kernel: one team of threads (a warp or a whole CTA) per
+// source, many sources in flight, sources pulled from a device counter.
+//
+// Per source (arxiv 1701.05975):
+//   forward  - parallel Dijkstra in settle batches (Sec. 3.2, Algorithm 2 with
+//              the work-efficient frontier queue of Algorithms 4-5).  A batch
+//              is every candidate u with D(u) < Delta', where Delta' <=
+//              Delta_i = min_{u in U} (D(u) + Delta_node(u)) (Eq. 2, strict
+//              test of Eq. 4); optionally also every u with
+//              D(u) < min_{U} D + Delta_node(u) (strict IN test).  Candidates
+//              are split into a near queue (D < split) and a far queue; only
+//              the near queue is scanned per phase.  The batches are the
+//              levels S / ends of Algorithm 1.
+//              sigma(v) is pulled from v's predecessors when v's batch is
+//              expanded: they all settled in earlier batches, so their sigma
+//              is final.  The same adjacency walk relaxes v's neighbours with
+//              atomicMin on the distance word (replacing the per-vertex locks
+//              of Sec. 3.2).
+//   backward - Algorithm 3: levels in reverse; for w in a level,
+//              delta(w) = sigma(w) * sum_{successors v} c(v) with
+//              c(v) = (1 + delta(v)) / sigma(v) kept in sigma's slot; delta(w)
+//              is added to BC with an FP64 atomic.
+// Every CSR walk uses a load-balanced edge-parallel chunk: the team takes up
+// to TEAM frontier vertices, scans their degrees and spreads the chunk's edges
+// evenly over its threads, so hubs never serialise one thread or warp.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "bc_common.h"
+
+namespace bcgpu {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+template <typename D>
+__device__ __forceinline__ D dinf() {
+  return ~D(0);
+}
+
+__device__ __forceinline__ uint32_t ldcg(const uint32_t* p) { return __ldcg(p); }
+__device__ __forceinline__ uint64_t ldcg(const uint64_t* p) {
+  return (uint64_t)__ldcg(reinterpret_cast<const unsigned long long*>(p));
+}
+__device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
+
+__device__ __forceinline__ uint32_t atomic_min_d(uint32_t* p, uint32_t v) { return atomicMin(p, v); }
+__device__ __forceinline__ uint64_t atomic_min_d(uint64_t* p, uint64_t v) {
+  return (uint64_t)atomicMin(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
+}
+
+template <typename D>
+__device__ __forceinline__ D sat_add(D a, uint64_t b) {
+  uint64_t lim = (uint64_t)dinf<D>() - 1;
+  uint64_t aa = (uint64_t)a;
+  if (aa >= lim || b >= lim - aa) return (D)lim;
+  return (D)(aa + b);
+}
+
+template <typename D>
+__device__ __forceinline__ D shfl_xor_d(D x, int o) {
+  return __shfl_xor_sync(FULL, x, o);
+}
+
+template <typename D>
+__device__ __forceinline__ D dmin(D a, D b) {
+  return a < b ? a : b;
+}
+
+template <typename D, int TEAM>
+struct TeamShared {
+  uint32_t src_idx;
+  uint32_t near_len, far_len, S_len, nlev;
+  int stop;
+  D split;
+  uint32_t off[TEAM + 1];
+  uint32_t vtx[TEAM];
+  unsigned long long rs[TEAM];
+  D dv[TEAM];
+  double acc[TEAM];
+  double sv[TEAM];
+  D red[2 * (TEAM / 32) + 2];
+  uint32_t scan[TEAM / 32 + 1];
+};
+
+template <int TEAM>
+__device__ __forceinline__ void team_sync() {
+  if constexpr (TEAM == 32) {
+    __syncwarp();
+  } else {
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(FULL, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+// Exclusive prefix sum over the team; *total receives the team-wide sum.
+// Every thread of the team must call it.
+template <int TEAM>
+__device__ __forceinline__ uint32_t team_excl_scan(uint32_t x, uint32_t* total, uint32_t* scratch) {
+  uint32_t inc = warp_incl_scan(x);
+  if constexpr (TEAM == 32) {
+    *total = __shfl_sync(FULL, inc, 31);
+    return inc - x;
+  } else {
+    constexpr int NW = TEAM / 32;
+    const int w = (threadIdx.x % TEAM) >> 5, lane = threadIdx.x & 31;
+    if (lane == 31) scratch[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+      uint32_t v = lane < NW ? scratch[lane] : 0u;
+      uint32_t vi = warp_incl_scan(v);
+      if (lane < NW) scratch[lane] = vi - v;
+      if (lane == NW - 1) scratch[NW] = vi;
+    }
+    __syncthreads();
+    *total = scratch[NW];
+    uint32_t r = scratch[w] + inc - x;
+    __syncthreads();
+    return r;
+  }
+}
+
+// Team-wide minimum of two values at once.
+template <typename D, int TEAM>
+__device__ __forceinline__ void team_min2(D& a, D& b, D* scratch) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a = dmin(a, shfl_xor_d(a, o));
+    b = dmin(b, shfl_xor_d(b, o));
+  }
+  if constexpr (TEAM > 32) {
+    constexpr int NW = TEAM / 32;
+    const int w = (threadIdx.x % TEAM) >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+      scratch[w] = a;
+      scratch[NW + w] = b;
+    }
+    __syncthreads();
+    if (w == 0) {
+      D x = lane < NW ? scratch[lane] : dinf<D>();
+      D y = lane < NW ? scratch[NW + lane] : dinf<D>();
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        x = dmin(x, shfl_xor_d(x, o));
+        y = dmin(y, shfl_xor_d(y, o));
+      }
+      if (lane == 0) {
+        scratch[2 * NW] = x;
+        scratch[2 * NW + 1] = y;
+      }
+    }
+    __syncthreads();
+    a = scratch[2 * NW];
+    b = scratch[2 * NW + 1];
+    __syncthreads();
+  }
+}
+
+template <typename D>
+struct Slab {
+  D* d;
+  double* sig;
+  uint32_t* S;
+  uint32_t* ends;
+  uint32_t* nearq;
+  uint32_t* farq;
+};
+
+template <typename D>
+__device__ __forceinline__ Slab<D> slab_at(const BatchArgs& a, uint32_t slot) {
+  char* base = a.slabs + (uint64_t)slot * a.lay.stride;
+  Slab<D> s;
+  s.d = reinterpret_cast<D*>(base + a.lay.off_d);
+  s.sig = reinterpret_cast<double*>(base + a.lay.off_sig);
+  s.S = reinterpret_cast<uint32_t*>(base + a.lay.off_S);
+  s.ends = reinterpret_cast<uint32_t*>(base + a.lay.off_ends);
+  s.nearq = reinterpret_cast<uint32_t*>(base + a.lay.off_near);
+  s.farq = reinterpret_cast<uint32_t*>(base + a.lay.off_far);
+  return s;
+}
+
+// Load a chunk [base, base + cnt) of a level list into shared memory and scan
+// the degrees.  Returns the chunk's edge total (uniform over the team).
+template <typename D, int TEAM>
+__device__ __forceinline__ uint32_t load_chunk(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, TEAM>& sh,
+                                               uint32_t base, uint32_t cnt, int t, bool want_sigma) {
+  uint32_t deg = 0;
+  if ((uint32_t)t < cnt) {
+    uint32_t v = ldcg(&sl.S[base + t]);
+    uint64_t r0 = __ldg(&a.g.row_ptr[v]);
+    uint64_t r1 = __ldg(&a.g.row_ptr[v + 1]);
+    deg = (uint32_t)(r1 - r0);
+    sh.vtx[t] = v;
+    sh.rs[t] = r0;
+    sh.dv[t] = ldcg(&sl.d[v]);
+    sh.acc[t] = 0.0;
+    if (want_sigma) sh.sv[t] = ldcg(&sl.sig[v]);
+  }
+  uint32_t total;
+  uint32_t ex = team_excl_scan<TEAM>(deg, &total, sh.scan);
+  if ((uint32_t)t < cnt) sh.off[t] = ex;
+  if (t == 0) sh.off[cnt] = total;
+  team_sync<TEAM>();
+  return total;
+}
+
+// Index i of the chunk vertex owning chunk edge e: off[i] <= e < off[i + 1].
+template <int TEAM>
+__device__ __forceinline__ uint32_t owner_of(const uint32_t* off, uint32_t cnt, uint32_t e) {
+  uint32_t lo = 0, hi = cnt;
+  while (hi - lo > 1) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (off[mid] <= e) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Forward expansion of the batch S[f0, f1): sigma pull + relaxation.
+template <typename D, int TEAM>
+__device__ void expand_forward(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, TEAM>& sh, uint32_t f0,
+                               uint32_t f1, uint32_t s, int t, D split, unsigned long long& relax,
+                               unsigned long long& scanned) {
+  const D INF = dinf<D>();
+  for (uint32_t base = f0; base < f1; base += TEAM) {
+    const uint32_t cnt = min((uint32_t)TEAM, f1 - base);
+    const uint32_t total = load_chunk<D, TEAM>(a, sl, sh, base, cnt, t, false);
+    scanned += (t == 0) ? total : 0;
+    for (uint32_t e = t; e < total; e += TEAM) {
+      const uint32_t i = owner_of<TEAM>(sh.off, cnt, e);
+      const uint2 ent = __ldg(&a.g.adj[sh.rs[i] + (e - sh.off[i])]);
+      const uint32_t u = ent.x;
+      const D w = (D)ent.y;
+      const D dvi = sh.dv[i];
+      const D du = ldcg(&sl.d[u]);
+      if (du != INF && du + w == dvi) {
+        // u is a shortest-path predecessor of v (settled in an earlier batch)
+        atomicAdd(&sh.acc[i], ldcg(&sl.sig[u]));
+      } else {
+        const D nd = dvi + w;
+        if (nd < du) {
+          ++relax;
+          const D old = atomic_min_d(&sl.d[u], nd);
+          if (nd < old) {
+            if (old == INF) {
+              if (nd < split) {
+                sl.nearq[atomicAdd(&sh.near_len, 1u)] = u;
+              } else {
+                sl.farq[atomicAdd(&sh.far_len, 1u)] = u;
+              }
+            } else if (old >= split && nd < split) {
+              sl.nearq[atomicAdd(&sh.near_len, 1u)] = u;
+            }
+          }
+        }
+      }
+    }
+    team_sync<TEAM>();
+    if ((uint32_t)t < cnt && sh.vtx[t] != s) sl.sig[sh.vtx[t]] = sh.acc[t];
+    team_sync<TEAM>();
+  }
+}
+
+// Backward (Algorithm 3) over one level S[f0, f1).
+template <typename D, int TEAM>
+__device__ void accumulate_level(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, TEAM>& sh, uint32_t f0,
+                                 uint32_t f1, int t, unsigned long long& scanned) {
+  const D INF = dinf<D>();
+  const bool edges = a.ebc != nullptr;
+  for (uint32_t base = f0; base < f1; base += TEAM) {
+    const uint32_t cnt = min((uint32_t)TEAM, f1 - base);
+    const uint32_t total = load_chunk<D, TEAM>(a, sl, sh, base, cnt, t, edges);
+    scanned += (t == 0) ? total : 0;
+    for (uint32_t e = t; e < total; e += TEAM) {
+      const uint32_t i = owner_of<TEAM>(sh.off, cnt, e);
+      const uint64_t entry = sh.rs[i] + (e - sh.off[i]);
+      const uint2 ent = __ldg(&a.g.adj[entry]);
+      const uint32_t u = ent.x;
+      const D du = ldcg(&sl.d[u]);
+      if (du != INF && du == sh.dv[i] + (D)ent.y) {
+        // u is a successor: its coefficient c(u) is final (later level)
+        const double cu = ldcg(&sl.sig[u]);
+        atomicAdd(&sh.acc[i], cu);
+        if (edges) atomicAdd(&a.ebc[entry], sh.sv[i] * cu);
+      }
+    }
+    team_sync<TEAM>();
+    if ((uint32_t)t < cnt) {
+      const uint32_t v = sh.vtx[t];
+      const double sg = ldcg(&sl.sig[v]);
+      const double delta = sg * sh.acc[t];
+      sl.sig[v] = (1.0 + delta) / sg;
+      atomicAdd(&a.bc[v], delta);
+    }
+    team_sync<TEAM>();
+  }
+}
+
+// Returns false when the source hit the phase cap (its slab is then dirty).
+template <typename D, int TEAM>
+__device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, TEAM>& sh, uint32_t s, int t) {
+  const D INF = dinf<D>();
+  unsigned long long relax = 0, scanned = 0;
+  uint64_t phases = 0, refills = 0;
+  // Algorithm 1 / 4: d = INF everywhere already (slab invariant)
+  if (t == 0) {
+    sl.d[s] = 0;
+    sl.sig[s] = 1.0;
+    sl.S[0] = s;
+    sl.ends[0] = 0;
+    sl.ends[1] = 1;
+    sh.near_len = 0;
+    sh.far_len = 0;
+    sh.S_len = 1;
+    sh.nlev = 1;
+    sh.stop = 0;
+    sh.split = sat_add<D>((D)0, a.width);
+  }
+  team_sync<TEAM>();
+  uint32_t f0 = 0, f1 = 1;
+  for (;;) {
+    const D split0 = sh.split;
+    expand_forward<D, TEAM>(a, sl, sh, f0, f1, s, t, split0, relax, scanned);
+    // refill the near queue from the far queue when it runs dry
+    while (sh.near_len == 0 && sh.far_len > 0) {
+      const D old = sh.split;
+      const uint32_t fl = sh.far_len;
+      D lo = INF, dummy = INF;
+      for (uint32_t base = 0; base < fl; base += TEAM) {
+        const uint32_t j = base + t;
+        if (j < fl) {
+          const D du = ldcg(&sl.d[ldcg(&sl.farq[j])]);
+          if (du >= old) lo = dmin(lo, du);
+        }
+      }
+      team_min2<D, TEAM>(lo, dummy, sh.red);
+      const D ns = (lo == INF) ? old : sat_add<D>(lo, a.width);
+      uint32_t kept = 0;
+      for (uint32_t base = 0; base < fl; base += TEAM) {
+        const uint32_t j = base + t;
+        uint32_t u = 0, keep = 0;
+        if (j < fl) {
+          u = ldcg(&sl.farq[j]);
+          const D du = ldcg(&sl.d[u]);
+          if (du >= old) {  // below the old split: already handled by the near queue
+            if (du < ns) {
+              sl.nearq[atomicAdd(&sh.near_len, 1u)] = u;
+            } else {
+              keep = 1;
+            }
+          }
+        }
+        uint32_t ktot;
+        const uint32_t kx = team_excl_scan<TEAM>(keep, &ktot, sh.scan);
+        if (TEAM == 32) __syncwarp();
+        if (keep) sl.farq[kept + kx] = u;
+        kept += ktot;
+      }
+      team_sync<TEAM>();
+      if (t == 0) {
+        sh.far_len = kept;
+        sh.split = ns;
+      }
+      ++refills;
+      if (phases + refills > a.phase_cap && t == 0) sh.stop = 1;
+      team_sync<TEAM>();
+      if (sh.stop) break;
+    }
+    if (sh.stop || sh.near_len == 0) break;
+    // threshold: Delta' = min(min_near (D + Delta_node), split) <= Delta_i
+    const uint32_t nl = sh.near_len;
+    const D split = sh.split;
+    D out = INF, dm = INF;
+    for (uint32_t base = 0; base < nl; base += TEAM) {
+      const uint32_t j = base + t;
+      if (j < nl) {
+        const uint32_t u = ldcg(&sl.nearq[j]);
+        const D du = ldcg(&sl.d[u]);
+        out = dmin(out, (D)(du + (D)__ldg(&a.g.dnode[u])));
+        dm = dmin(dm, du);
+      }
+    }
+    team_min2<D, TEAM>(out, dm, sh.red);
+    const D thr = dmin(out, split);
+    // settle (strict) and compact the near queue in place
+    const uint32_t S0 = sh.S_len;
+    uint32_t nset = 0, kept = 0;
+    for (uint32_t base = 0; base < nl; base += TEAM) {
+      const uint32_t j = base + t;
+      uint32_t u = 0, take = 0, valid = j < nl;
+      if (valid) {
+        u = ldcg(&sl.nearq[j]);
+        const D du = ldcg(&sl.d[u]);
+        take = du < thr;
+        if (a.settle_in && !take) take = du < (D)(dm + (D)__ldg(&a.g.dnode[u]));
+      }
+      uint32_t stot;
+      const uint32_t sx = team_excl_scan<TEAM>(take, &stot, sh.scan);
+      if (TEAM == 32) __syncwarp();
+      if (take) sl.S[S0 + nset + sx] = u;
+      if (valid && !take) sl.nearq[kept + (j - base) - sx] = u;
+      const uint32_t ccount = min((uint32_t)TEAM, nl - base);
+      nset += stot;
+      kept += ccount - stot;
+    }
+    ++phases;
+    team_sync<TEAM>();
+    if (t == 0) {
+      sh.near_len = kept;
+      sh.S_len = S0 + nset;
+      sh.nlev += 1;
+      sl.ends[sh.nlev] = S0 + nset;
+      if (phases + refills > a.phase_cap) sh.stop = 1;
+    }
+    team_sync<TEAM>();
+    if (sh.stop) break;
+    f0 = S0;
+    f1 = S0 + nset;
+  }
+  const bool failed = sh.stop != 0;
+  if (failed) {
+    if (t == 0) atomicCAS(a.err, DEV_OK, DEV_ERR_TIMEOUT);
+    // every touched vertex is settled (S), near or far: restore d = INF there
+    const uint32_t sl_n = sh.S_len, nl_n = sh.near_len, fl_n = sh.far_len;
+    for (uint32_t j = t; j < sl_n; j += TEAM) sl.d[ldcg(&sl.S[j])] = INF;
+    for (uint32_t j = t; j < nl_n; j += TEAM) sl.d[ldcg(&sl.nearq[j])] = INF;
+    for (uint32_t j = t; j < fl_n; j += TEAM) sl.d[ldcg(&sl.farq[j])] = INF;
+  } else if (a.flags & RUN_FORWARD_ONLY) {
+    if (t == 0 && a.debug_out) {
+      a.debug_out[0] = sh.nlev;
+      a.debug_out[1] = sh.S_len;
+    }
+  } else {
+    const uint32_t nlev = sh.nlev;
+    for (int lev = (int)nlev - 1; lev >= 1; --lev) {
+      const uint32_t b0 = ldcg(&sl.ends[lev]);
+      const uint32_t b1 = ldcg(&sl.ends[lev + 1]);
+      accumulate_level<D, TEAM>(a, sl, sh, b0, b1, t, scanned);
+    }
+    // restore the slab invariant: d = INF on every vertex this source reached
+    const uint32_t n_reached = sh.S_len;
+    for (uint32_t j = t; j < n_reached; j += TEAM) sl.d[ldcg(&sl.S[j])] = INF;
+  }
+  if (a.stats) {
+    // relax is per thread; the rest are uniform (counted once)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) relax += __shfl_xor_sync(FULL, relax, o);
+    if ((t & 31) == 0) atomicAdd(&a.stats[STAT_RELAX], relax);
+    if (t == 0) {
+      atomicAdd(&a.stats[STAT_SOURCES], 1ull);
+      atomicAdd(&a.stats[STAT_PHASES], (unsigned long long)phases);
+      atomicAdd(&a.stats[STAT_REFILLS], (unsigned long long)refills);
+      atomicAdd(&a.stats[STAT_REACHED], (unsigned long long)sh.S_len);
+      atomicAdd(&a.stats[STAT_ENTRIES], scanned);
+    }
+  }
+  team_sync<TEAM>();
+  return !failed;
+}
+
+
+template <typename D, int TEAM, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) bc_batched_kernel(const BatchArgs a) {
+  static_assert(TEAM == 32 || TEAM == BLOCK, "a CTA holds either warp teams or one team");
+  constexpr int NTEAMS = BLOCK / TEAM;
+  __shared__ TeamShared<D, TEAM> shared_teams[NTEAMS];
+  const int team = threadIdx.x / TEAM;
+  const int t = threadIdx.x % TEAM;
+  const uint32_t slot = blockIdx.x * NTEAMS + team;
+  if (slot >= a.nslots) return;  // a whole team leaves together
+  TeamShared<D, TEAM>& sh = shared_teams[team];
+  const Slab<D> sl = slab_at<D>(a, slot);
+  for (;;) {
+    if (t == 0) sh.src_idx = atomicAdd(a.counter, 1u);
+    team_sync<TEAM>();
+    const uint32_t idx = sh.src_idx;
+    team_sync<TEAM>();
+    if (idx >= a.k) break;
+    const uint32_t s = __ldg(&a.sources[idx]);
+    if (s >= a.g.n) {
+      if (t == 0) atomicCAS(a.err, DEV_OK, DEV_ERR_INVALID);
+      continue;
+    }
+    const bool ok = run_source<D, TEAM>(a, sl, sh, s, t);
+    if (!ok || (a.flags & RUN_FORWARD_ONLY)) break;
+  }
+}
+
+template <typename D, int TEAM, int BLOCK>
+cudaError_t launch_t(const BatchArgs& a, int grid, cudaStream_t st) {
+  bc_batched_kernel<D, TEAM, BLOCK><<<grid, BLOCK, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename D>
+cudaError_t launch_d(const BatchArgs& a, int team, int grid, cudaStream_t st) {
+  switch (team) {
+    case 32: return launch_t<D, 32, 256>(a, grid, st);
+    case 128: return launch_t<D, 128, 128>(a, grid, st);
+    case 256: return launch_t<D, 256, 256>(a, grid, st);
+    case 512: return launch_t<D, 512, 512>(a, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename D>
+cudaError_t occ_d(int team, int* out) {
+  switch (team) {
+    case 32: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, bc_batched_kernel<D, 32, 256>, 256, 0);
+    case 128: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, bc_batched_kernel<D, 128, 128>, 128, 0);
+    case 256: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, bc_batched_kernel<D, 256, 256>, 256, 0);
+    case 512: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, bc_batched_kernel<D, 512, 512>, 512, 0);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+int batched_block_threads(int team) { return team == 32 ? 256 : team; }
+
+cudaError_t launch_batched(const BatchArgs& a, int dist_bits, int team, int grid, cudaStream_t st) {
+  if (grid <= 0) return cudaSuccess;
+  return dist_bits == 32 ? launch_d<uint32_t>(a, team, grid, st) : launch_d<uint64_t>(a, team, grid, st);
+}
+
+cudaError_t batched_occupancy(int dist_bits, int team, int* blocks_per_sm) {
+  return dist_bits == 32 ? occ_d<uint32_t>(team, blocks_per_sm) : occ_d<uint64_t>(team, blocks_per_sm);
+}
+
+}  // namespace bcgpu

@@ -1,0 +1,95 @@
+// Internal declarations shared by the CUDA translation units of libbcgpu.
+// Not part of the public ABI (that is include/bcgpu.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace bcgpu {
+
+// Graph as the kernels see it (Sec. 3.1: CSR plus a parallel weight array,
+// here interleaved as one 8-byte {col, w} record per entry).
+struct GraphDev {
+  uint32_t n;
+  uint64_t nnz;
+  const uint64_t* row_ptr;  // [n + 1]
+  const uint2* adj;         // [nnz] {neighbour, weight}
+  const uint32_t* dnode;    // [n] Delta_node(v) = min incident weight (UINT32_MAX if isolated)
+};
+
+// Byte offsets of the per-source arrays inside one slab (one slab per source
+// in flight).  d: distances (all INF between sources), sig: sigma during the
+// forward pass and the coefficient c = (1 + delta) / sigma during the backward
+// pass, S: settle order (the level lists of Algorithm 1's S/ends), ends: level
+// boundaries, nearq / farq: candidate queues (reached, unsettled vertices
+// below / at or above the current split).
+struct SlabLayout {
+  uint64_t stride;
+  uint64_t off_d, off_sig, off_S, off_ends, off_near, off_far;
+};
+
+enum : uint32_t {
+  RUN_FORWARD_ONLY = 1u,  // stop after distances / sigma / levels (test hook)
+};
+
+enum : int {
+  DEV_OK = 0,
+  DEV_ERR_INVALID = 1,  // out-of-range source
+  DEV_ERR_TIMEOUT = 4,  // phase cap hit
+};
+
+// Per-run counters (summed over sources).
+enum : int {
+  STAT_SOURCES = 0,
+  STAT_PHASES,
+  STAT_REFILLS,
+  STAT_REACHED,
+  STAT_RELAX,
+  STAT_ENTRIES,
+  STAT_COUNT
+};
+
+struct BatchArgs {
+  GraphDev g;
+  const uint32_t* sources;
+  uint32_t k;
+  uint32_t* counter;  // [0]: next source index (zeroed before launch)
+  double* bc;         // [n] raw sum of delta (scale applied afterwards)
+  double* ebc;        // [nnz] raw per-entry shares, or nullptr
+  char* slabs;
+  SlabLayout lay;
+  uint32_t nslots;
+  uint64_t width;      // near/far split width
+  uint32_t settle_in;  // apply the strict IN criterion too
+  uint64_t phase_cap;  // cap on phases + refills per source
+  int* err;            // DEV_* status word
+  unsigned long long* stats;  // [STAT_COUNT] or nullptr
+  uint32_t flags;      // RUN_*
+  uint32_t* debug_out; // RUN_FORWARD_ONLY: [0] = levels, [1] = reached
+};
+
+// Launchers (bc_batched.cu).  team: 32, 128, 256 or 512 threads per source.
+cudaError_t launch_batched(const BatchArgs& a, int dist_bits, int team, int grid, cudaStream_t st);
+int batched_block_threads(int team);
+cudaError_t batched_occupancy(int dist_bits, int team, int* blocks_per_sm);
+
+// Graph preparation and small helpers (bc_prep.cu).
+cudaError_t launch_prep(uint32_t n, uint64_t nnz, const uint64_t* row_ptr, const uint32_t* col, const uint32_t* w,
+                        uint2* adj, uint32_t* dnode, cudaStream_t st);
+cudaError_t launch_fill_u64(uint64_t* p, uint64_t count, uint64_t value, cudaStream_t st);
+cudaError_t launch_scale(double* p, uint64_t count, double scale, cudaStream_t st);
+cudaError_t launch_check_sources(const uint32_t* src, uint32_t k, uint32_t n, int* err, cudaStream_t st);
+
+// Plain form (bc_plain.cu): one source at a time over the whole GPU.
+struct PlainWork;
+PlainWork* plain_create(uint32_t n, int dist_bits, cudaError_t* e);
+void plain_destroy(PlainWork* w);
+uint64_t plain_bytes(uint32_t n, int dist_bits);
+// Runs sources[0..k) (HOST list) one after another; adds raw delta into bc.
+// Returns DEV_* status through *dev_status.
+cudaError_t plain_run(PlainWork* w, const GraphDev& g, int dist_bits, const uint32_t* host_sources, uint32_t k,
+                      double* bc, uint64_t width, uint32_t settle_in, uint64_t phase_cap, int sm_count,
+                      cudaStream_t st, int* dev_status, unsigned long long* host_stats);
+
+}  // namespace bcgpu

@@ -1,0 +1,203 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Tolerance (BASELINE target): distances bit-exact; sigma exact (integers
+below 2^53); BC zero exactly where the oracle's is zero, else relative error
+<= 1e-9 per vertex.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1701_05975_gb300 as bc
+from paper_1701_05975_gb300 import gen
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-9
+U64MAX = np.iinfo(np.uint64).max
+
+
+def assert_bc_close(got, want, rel=REL):
+    got = np.asarray(got)
+    want = np.asarray(want)
+    zg, zw = got == 0, want == 0
+    assert np.array_equal(zg, zw), f"zero pattern differs at {np.flatnonzero(zg != zw)[:10]}"
+    nz = ~zw
+    if nz.any():
+        err = np.abs(got[nz] - want[nz]) / np.abs(want[nz])
+        assert err.max() <= rel, f"max rel err {err.max():.3e} at {np.flatnonzero(nz)[err.argmax()]}"
+
+
+@pytest.fixture(autouse=True)
+def default_config():
+    c0 = bc.bc_get_config()
+    yield
+    bc.bc_set_config(c0)
+
+
+def graph(n, edges):
+    u, v, w = zip(*edges) if edges else ((), (), ())
+    return gen.csr_from_undirected(n, np.array(u, np.int64), np.array(v, np.int64), np.array(w, np.int64))
+
+
+CONFIGS = [
+    dict(team_threads=32, settle_in=1, bucket_width=0),
+    dict(team_threads=128, settle_in=2, bucket_width=1),
+    dict(team_threads=256, settle_in=1, bucket_width=3),
+    dict(team_threads=512, settle_in=2, bucket_width=1 << 40),
+]
+
+
+@pytest.mark.parametrize("cfg", CONFIGS, ids=lambda c: f"team{c['team_threads']}-in{c['settle_in']}-w{c['bucket_width']}")
+def test_small_random_graphs_all_team_shapes(cfg):
+    bc.bc_set_config(**cfg)
+    rng = np.random.default_rng(101)
+    for i in range(40):
+        n = int(rng.integers(1, 70))
+        g = gen.random_small_graph(n, float(rng.choice([0.05, 0.2, 0.6])), 1, int(rng.choice([1, 3, 50])), rng)
+        src = np.arange(n, dtype=np.uint32)
+        with bc.Graph(g) as G:
+            assert_bc_close(G.compute(src, 1.0), oracle.bc(g, src, 1.0))
+            for s in (0, n // 2, n - 1):
+                d, sg, lev = G.sssp_debug(s)
+                d_ref, sg_ref, _ = oracle.sssp(g, s)
+                assert np.array_equal(d, d_ref)
+                assert np.array_equal(sg, sg_ref)
+
+
+def test_fig1a_strict_criterion_on_gpu():
+    # Sec. 3.2: the correct sigma of v3 is 2; Eq. 3 would give 1
+    g = graph(4, [(0, 1, 1), (1, 2, 1), (0, 2, 2), (2, 3, 1)])
+    for team in (32, 256):
+        for si in (1, 2):
+            bc.bc_set_config(team_threads=team, settle_in=si)
+            with bc.Graph(g) as G:
+                d, sg, lev = G.sssp_debug(0)
+            assert list(d) == [0, 1, 2, 3]
+            assert list(sg) == [1, 1, 2, 2]
+            assert lev[1] < lev[2] < lev[3]
+
+
+def test_edge_cases():
+    # n = 1, isolated vertices, two components, self-loops, parallel edges
+    cases = [
+        graph(1, []),
+        graph(2, []),
+        graph(2, [(0, 1, 7)]),
+        graph(6, [(0, 1, 2), (1, 2, 2), (3, 4, 1), (4, 5, 1), (3, 5, 2)]),
+        gen.csr_from_directed(4, [0, 1, 0, 1, 1, 2, 2, 3, 2, 3], [1, 0, 1, 0, 2, 1, 3, 2, 2, 3],
+                              [2, 2, 2, 2, 1, 1, 1, 1, 1, 4]),
+    ]
+    for g in cases:
+        src = np.arange(g.n, dtype=np.uint32)
+        for team in (32, 512):
+            bc.bc_set_config(team_threads=team)
+            with bc.Graph(g) as G:
+                assert_bc_close(G.compute(src, 0.5), oracle.bc(g, src, 0.5))
+                assert np.all(G.compute(np.zeros(0, np.uint32), 0.5) == 0)
+
+
+def test_levels_are_legal_and_distances_exact_on_er1k():
+    g, src, scale = gen.workload_er1k()
+    with bc.Graph(g) as G:
+        rows, cols, ws = g.edges()
+        for s in (0, 17, 1023):
+            d, sg, lev = G.sssp_debug(s)
+            d_ref, sg_ref, _ = oracle.sssp(g, s)
+            assert np.array_equal(d, d_ref)
+            assert np.array_equal(sg, sg_ref)
+            dag = (d[rows] != U64MAX) & (d[rows] + ws.astype(np.uint64) == d[cols])
+            assert np.all(lev[rows[dag]] < lev[cols[dag]])
+
+
+@pytest.mark.parametrize("team", [32, 128, 256, 512])
+def test_er1k_workload_full(team):
+    bc.bc_set_config(team_threads=team)
+    g, src, scale = gen.workload_er1k()
+    want = oracle.bc(g, src, scale, nthreads=8)
+    with bc.Graph(g) as G:
+        assert_bc_close(G.compute(src, scale), want)
+
+
+def test_plain_mode_matches_oracle():
+    g = gen.er_graph(400, 2400, 1, 100, seed=5)
+    src = np.arange(0, g.n, 7, dtype=np.uint32)
+    bc.bc_set_config(mode=bc.BC_MODE_PLAIN)
+    with bc.Graph(g) as G:
+        assert_bc_close(G.compute(src, 0.5), oracle.bc(g, src, 0.5))
+
+
+def test_ba65k_sampled_sources():
+    g, _, _ = gen.workload_ba65k()
+    src = gen.sample_sources(g.n, 192, seed=3)
+    want = oracle.bc(g, src, 1.0, nthreads=8)
+    with bc.Graph(g) as G:
+        for team in (32, 256):
+            bc.bc_set_config(team_threads=team)
+            assert_bc_close(G.compute(src, 1.0), want)
+        d, sg, _ = G.sssp_debug(int(src[0]))
+        d_ref, sg_ref, _ = oracle.sssp(g, int(src[0]))
+        assert np.array_equal(d, d_ref) and np.array_equal(sg, sg_ref)
+
+
+def test_linearity_duplicates_and_repeatability():
+    g = gen.ba_graph(3000, 3, 1, 50, seed=9)
+    a = np.arange(0, 3000, 5, dtype=np.uint32)
+    b = np.arange(1, 3000, 7, dtype=np.uint32)
+    with bc.Graph(g) as G:
+        ab = G.compute(np.concatenate([a, b]), 1.0)
+        sep = G.compute(a, 1.0) + G.compute(b, 1.0)
+        np.testing.assert_allclose(ab, sep, rtol=1e-11, atol=0)
+        one = G.compute(np.array([11], np.uint32), 1.0)
+        two = G.compute(np.array([11, 11], np.uint32), 1.0)
+        np.testing.assert_allclose(two, 2 * one, rtol=1e-13)
+        r1 = G.compute(a, 0.5)
+        r2 = G.compute(a, 0.5)
+        np.testing.assert_allclose(r1, r2, rtol=1e-12)
+
+
+def test_edge_bc_matches_oracle():
+    g = gen.er_graph(300, 1200, 1, 5, seed=12)
+    src = np.arange(g.n, dtype=np.uint32)
+    with bc.Graph(g) as G:
+        ebc, vbc = G.edge_compute(src, 0.5)
+    assert_bc_close(ebc, oracle.edge_bc(g, src, 0.5))
+    assert_bc_close(vbc, oracle.bc(g, src, 0.5))
+
+
+def test_errors_and_timeout_recovery():
+    g = gen.er_graph(500, 2000, 1, 30, seed=4)
+    src = np.arange(50, dtype=np.uint32)
+    with bc.Graph(g) as G:
+        with pytest.raises(bc.BCError) as ei:
+            G.compute(np.array([0, 500], np.uint32), 1.0)
+        assert ei.value.code == bc.BC_ERR_INVALID
+        bc.bc_set_config(phase_cap=3)
+        with pytest.raises(bc.BCError) as ei:
+            G.compute(src, 1.0)
+        assert ei.value.code == bc.BC_ERR_TIMEOUT
+        bc.bc_set_config(phase_cap=0)
+        assert_bc_close(G.compute(src, 1.0), oracle.bc(g, src, 1.0))
+
+
+def test_async_with_torch_buffers():
+    torch = pytest.importorskip("torch")
+    g = gen.er_graph(2000, 10000, 1, 100, seed=6)
+    src = np.arange(0, g.n, 3, dtype=np.uint32)
+    want = oracle.bc(g, src, 0.25)
+    dev = torch.device("cuda:0")
+    d_src = torch.from_numpy(src.astype(np.int32)).to(dev)
+    d_out = torch.empty(g.n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.Stream()
+    with bc.Graph(g) as G:
+        with torch.cuda.stream(stream):
+            bc.bc_compute_async(G.handle, d_src.data_ptr(), len(src), 0.25, d_out.data_ptr(), stream.cuda_stream)
+        bc.bc_sync_status(G.handle, stream.cuda_stream)
+        assert_bc_close(d_out.cpu().numpy(), want)
+        bad = torch.tensor([0, g.n + 5], dtype=torch.int32, device=dev)
+        bc.bc_compute_async(G.handle, bad.data_ptr(), 2, 1.0, d_out.data_ptr(), stream.cuda_stream)
+        with pytest.raises(bc.BCError) as ei:
+            bc.bc_sync_status(G.handle, stream.cuda_stream)
+        assert ei.value.code == bc.BC_ERR_INVALID
