@@ -1,0 +1,353 @@
+"""Benchmark: weighted betweenness centrality, GTEPS and HBM roofline.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--workload rmat20|ba65k|grid1024|er1k]
+                [--impl ours|reference] [--no-cpu-baseline] [--plain-sample S]
+
+One step = one batched BC run over the workload's whole source list (every
+step of the hot path: SSSP in strict settle batches, sigma, the backward
+dependency pass into BC), inputs resident in HBM.  GTEPS = sources x
+undirected edges / second (whole job: summed over ranks, weak scaling, one
+independent replica of the problem per GPU, no collective on the data path).
+Rank 0 prints one JSON line.  --impl reference times the CPU oracle instead
+(the reference arm of this tier), on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1701_05975_gb300 import gen  # noqa: E402
+
+WORKLOADS = {
+    "rmat20": ("R-MAT scale 20, edge factor 16, a=.57 b=.19 c=.19, symmetrised, weights U[1,255], "
+               "4096 uniform sources, scale 0.5 n/k", gen.workload_rmat20),
+    "ba65k": ("Barabasi-Albert n=65536, 4 edges per new vertex, weights U[1,1000], all sources, scale 0.5",
+              gen.workload_ba65k),
+    "grid1024": ("perturbed 1024x1024 4-neighbour grid, 5% edges removed, weights U[1,10000], 1024 sources",
+                 gen.workload_grid1024),
+    "er1k": ("Erdos-Renyi G(1024, 8192), weights U[1,100], all sources, scale 0.5", gen.workload_er1k),
+}
+
+# Algorithmic bytes per unit (the three-pass byte model of the method):
+# per CSR entry of a reached vertex 64 B (relax 16 + sigma 24 + backward 24),
+# per reached vertex 80 B.
+BYTES_PER_ENTRY = 64
+BYTES_PER_VERTEX = 80
+KERNEL_SRC = os.path.join(ROOT, "paper_1701_05975_gb300", "csrc", "bc_batched.cu")
+
+
+def reach_model(g, sources):
+    """Per-source reached vertices and reached CSR entries (component sizes)."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import connected_components
+
+    rows = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.row_ptr).astype(np.int64))
+    mat = sp.csr_matrix((np.ones(len(rows), np.int8), (rows, g.col.astype(np.int64))), shape=(g.n, g.n))
+    _, lab = connected_components(mat, directed=False)
+    comp_n = np.bincount(lab)
+    comp_e = np.bincount(lab, weights=np.diff(g.row_ptr).astype(np.float64))
+    ls = lab[sources.astype(np.int64)]
+    return comp_n[ls].astype(np.float64), comp_e[ls]
+
+
+def kernel_digest():
+    return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+
+
+def load_traffic(workload):
+    """DRAM bytes per launch of the batched kernel from the committed ncu
+    summary, or None when the summary is missing or the kernel changed since."""
+    path = os.path.join(ROOT, "profiles", f"bc_batched_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"kernel_sha256_16:\s*([0-9a-f]{16})", text)
+    t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m or not t or m.group(1) != kernel_digest():
+        return None
+    return float(t.group(1))
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        p = json.load(open(path))
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(g, sources, seconds_target=15.0, max_sample=4096):
+    """Time the CPU oracle (as it stands) on a bounded prefix of the source list."""
+    import oracle
+
+    cores = os.cpu_count() or 1
+    m = g.m
+    # probe a small prefix to size the sample
+    k = min(len(sources), max(cores, 8))
+    t0 = time.perf_counter()
+    oracle.bc(g, sources[:k], 1.0, nthreads=cores)
+    dt = time.perf_counter() - t0
+    if dt < seconds_target / 4 and k < len(sources):
+        k2 = int(min(len(sources), max_sample, k * max(1.0, (seconds_target / max(dt, 1e-3)) * 0.8)))
+        if k2 > k:
+            k = k2
+            t0 = time.perf_counter()
+            oracle.bc(g, sources[:k], 1.0, nthreads=cores)
+            dt = time.perf_counter() - t0
+    return {"value": k * m / dt / 1e9, "unit": "GTEPS", "cores": cores, "kind": "oracle",
+            "sample": f"first {k} of {len(sources)} sources of the same workload, {dt:.2f} s, "
+                      f"{cores} POSIX threads"}
+
+
+def run_reference(args, g, sources, scale, desc):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+
+    cores = os.cpu_count() or 1
+    m = g.m
+    # bounded sample per step: sized so the whole run stays within minutes
+    k = min(len(sources), max(cores, 16))
+    t0 = time.perf_counter()
+    oracle.bc(g, sources[:k], scale, nthreads=cores)
+    probe = time.perf_counter() - t0
+    budget_per_step = 150.0 / max(args.steps + args.warmup, 1)
+    if probe < budget_per_step / 2:
+        k = int(min(len(sources), k * max(1.0, 0.8 * budget_per_step / max(probe, 1e-3))))
+    for _ in range(args.warmup):
+        oracle.bc(g, sources[:k], scale, nthreads=cores)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.bc(g, sources[:k], scale, nthreads=cores)
+        times.append(time.perf_counter() - t0)
+    t = max(statistics.mean(times), 1e-9)
+    value = k * m / t / 1e9
+    line = {
+        "impl": "reference", "metric": "weighted-BC GTEPS (sources x undirected edges / s)", "value": value,
+        "unit": "GTEPS", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "n": g.n, "m": m, "sources_per_step": k, "sources_in_workload": len(sources)},
+        "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": cores, "kind": "oracle",
+                         "sample": f"first {k} of {len(sources)} sources per step"},
+        "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="rmat20", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--plain-sample", type=int, default=0, help="also time the plain form on this many sources")
+    ap.add_argument("--autotune", type=int, default=0, help="probe sources for the autotuner (0: off)")
+    args = ap.parse_args()
+
+    desc, maker = WORKLOADS[args.workload]
+    g, sources, scale = maker()
+    m = g.m
+
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, g, sources, scale, desc)
+        return
+
+    import torch
+
+    import paper_1701_05975_gb300 as bc
+
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    dev = torch.device("cuda", local)
+    G = bc.Graph(g)
+    if args.autotune:
+        G.autotune(sources[: args.autotune])
+    stream = torch.cuda.Stream(device=dev)
+    d_src = torch.from_numpy(sources.astype(np.int32)).to(dev)
+    d_out = torch.empty(g.n, dtype=torch.float64, device=dev)
+    k = len(sources)
+
+    def step():
+        bc.bc_compute_async(G.handle, d_src.data_ptr(), k, scale, d_out.data_ptr(), stream.cuda_stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        bc.bc_sync_status(G.handle, stream.cuda_stream)
+    st = G.stats()
+    barrier()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with torch.cuda.stream(stream):
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        t_end.record(stream)
+    torch.cuda.synchronize(dev)
+    bc.bc_sync_status(G.handle, stream.cuda_stream)
+    barrier()
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    launch_ms = [a.elapsed_time(b) for a, b in ev]
+    ms_step = total_ms / args.steps
+    if dist is not None:
+        tt = torch.tensor([ms_step], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_step = float(tt.item())
+    value = ws * k * m / (ms_step * 1e-3) / 1e9
+
+    # end to end through the public synchronous call: host sources in, host BC out
+    host_out = np.empty(g.n, np.float64)
+    e2e_times = []
+    for i in range(max(1, min(args.steps, 3)) + 1):
+        barrier()
+        t0 = time.perf_counter()
+        bc.bc_compute(G.handle, sources, scale, host_out)
+        dt = time.perf_counter() - t0
+        if i > 0:
+            e2e_times.append(dt)
+    e2e_s = statistics.mean(e2e_times)
+    if dist is not None:
+        tt = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+
+    # roofline of the dominant kernel (the batched kernel is > 99% of a step)
+    rn, re_ = reach_model(g, sources)
+    alg_bytes = float(BYTES_PER_ENTRY * re_.sum() + BYTES_PER_VERTEX * rn.sum())
+    launch_avg_s = statistics.mean(launch_ms) * 1e-3
+    achieved = alg_bytes / launch_avg_s / 1e9
+    peak, peak_kind = peaks()
+    traffic = load_traffic(args.workload)
+
+    line = {
+        "metric": "weighted-BC GTEPS (sources x undirected edges / s)",
+        "value": value, "unit": "GTEPS", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "n": g.n, "m": m, "nnz": g.nnz, "sources": k, "scale": scale,
+                   "l2": "inputs larger than L2 (CSR 251 MB + per-source slabs)",
+                   "team_threads": int(st.team_threads), "slots": int(st.slots),
+                   "bucket_width": int(st.bucket_width), "parallelism": f"replicas x{ws}"},
+        "e2e": {"value": ws * k * m / e2e_s / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": 4 * k,
+                "d2h_bytes_per_step": 8 * g.n},
+        "gpu_launches": 3 * args.steps,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "alg_bytes_per_launch": alg_bytes, "kernel": "bc_batched_kernel"},
+        "clocks": clk,
+        "run_stats": {"phases_per_source": st.phases / max(st.sources, 1),
+                      "refills_per_source": st.refills / max(st.sources, 1),
+                      "reached_per_source": st.reached / max(st.sources, 1)},
+    }
+    if args.plain_sample and rank == 0:
+        sub = sources[: args.plain_sample]
+        c0 = bc.bc_get_config()
+        bc.bc_set_config(mode=bc.BC_MODE_PLAIN)
+        out = np.empty(g.n, np.float64)
+        bc.bc_compute(G.handle, sub[:2], scale, out)
+        t0 = time.perf_counter()
+        bc.bc_compute(G.handle, sub, scale, out)
+        dt = time.perf_counter() - t0
+        bc.bc_set_config(c0)
+        line["plain"] = {"value": len(sub) * m / dt / 1e9, "unit": "GTEPS", "sources": len(sub)}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(g, sources)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    G.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

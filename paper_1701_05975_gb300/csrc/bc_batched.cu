@@ -273,7 +273,7 @@ __device__ void expand_forward(const BatchArgs& a, const Slab<D>& sl, TeamShared
 // Backward (Algorithm 3) over one level S[f0, f1).
 template <typename D, int TEAM>
 __device__ void accumulate_level(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, TEAM>& sh, uint32_t f0,
-                                 uint32_t f1, int t, unsigned long long& scanned) {
+                                 uint32_t f1, uint32_t s, int t, unsigned long long& scanned) {
   const D INF = dinf<D>();
   const bool edges = a.ebc != nullptr;
   for (uint32_t base = f0; base < f1; base += TEAM) {
@@ -299,7 +299,7 @@ __device__ void accumulate_level(const BatchArgs& a, const Slab<D>& sl, TeamShar
       const double sg = ldcg(&sl.sig[v]);
       const double delta = sg * sh.acc[t];
       sl.sig[v] = (1.0 + delta) / sg;
-      atomicAdd(&a.bc[v], delta);
+      if (v != s) atomicAdd(&a.bc[v], delta);
     }
     team_sync<TEAM>();
   }
@@ -440,11 +440,14 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
       a.debug_out[1] = sh.S_len;
     }
   } else {
+    // level 0 is the source: delta(s) is not part of BC, but with edge
+    // output its outgoing shortest-path edges still carry shares
     const uint32_t nlev = sh.nlev;
-    for (int lev = (int)nlev - 1; lev >= 1; --lev) {
+    const int last = a.ebc ? 0 : 1;
+    for (int lev = (int)nlev - 1; lev >= last; --lev) {
       const uint32_t b0 = ldcg(&sl.ends[lev]);
       const uint32_t b1 = ldcg(&sl.ends[lev + 1]);
-      accumulate_level<D, TEAM>(a, sl, sh, b0, b1, t, scanned);
+      accumulate_level<D, TEAM>(a, sl, sh, b0, b1, s, t, scanned);
     }
     // restore the slab invariant: d = INF on every vertex this source reached
     const uint32_t n_reached = sh.S_len;
