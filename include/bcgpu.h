@@ -54,6 +54,9 @@ extern "C" {
 
 /* ---- graph flags ------------------------------------------------------- */
 #define BC_UNDIRECTED_CHECK 0x1u /* verify that every (u -> v, w) entry has a (v -> u, w) twin */
+#define BC_RELABEL_DEGREE 0x2u   /* always store vertices internally in decreasing-degree order */
+#define BC_KEEP_ORDER 0x4u       /* never relabel (default: relabel when the top 1% of vertices by degree
+                                    hold more than 10% of the CSR entries) */
 
 /* ---- execution modes --------------------------------------------------- */
 #define BC_MODE_BATCHED 0u /* persistent launch: one team (warp or CTA) per source, many sources in flight */
@@ -99,7 +102,9 @@ const char *bc_last_error(void);
  * them and the caller keeps ownership.  Validation: n >= 1, row_ptr[0] = 0,
  * non-decreasing, row_ptr[n] = nnz, col_idx < n, w >= 1; with
  * BC_UNDIRECTED_CHECK also the symmetry of the entries.  Precomputes
- * Delta_node(v) = min incident weight (Sec. 3.2, before Eq. 2).
+ * Delta_node(v) = min incident weight (Sec. 3.2, before Eq. 2).  Internal
+ * vertex order is a layout choice only (see BC_RELABEL_DEGREE / BC_KEEP_ORDER):
+ * every input and output of this ABI uses the caller's vertex and entry ids.
  * On success *out holds an opaque handle that bc_graph_destroy releases.
  */
 int bc_graph_create(const uint64_t *row_ptr, const uint32_t *col_idx, const uint32_t *w, uint32_t n,
@@ -218,6 +223,8 @@ typedef struct bc_run_stats {
   uint32_t team_threads;
   uint32_t slots;
   uint64_t bucket_width;
+  uint64_t dag_edges;       /* shortest-path DAG edges recorded by the forward pass */
+  uint64_t pair_overflows;  /* sources whose DAG edge list overflowed (backward fell back to a CSR scan) */
 } bc_run_stats;
 
 int bc_last_run_stats(bc_graph_t g, bc_run_stats *out);

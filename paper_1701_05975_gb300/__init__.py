@@ -27,6 +27,8 @@ BC_ERR_TIMEOUT = 4
 BC_ERR_BUSY = 5
 BC_ERR_CANCELLED = 6
 BC_UNDIRECTED_CHECK = 1
+BC_RELABEL_DEGREE = 2
+BC_KEEP_ORDER = 4
 BC_MODE_BATCHED = 0
 BC_MODE_PLAIN = 1
 BC_REQ_QUEUED, BC_REQ_RUNNING, BC_REQ_DONE, BC_REQ_FAILED, BC_REQ_CANCELLED = range(5)
@@ -56,7 +58,8 @@ class bc_run_stats(ctypes.Structure):
     _fields_ = [("sources", ctypes.c_uint64), ("phases", ctypes.c_uint64), ("refills", ctypes.c_uint64),
                 ("reached", ctypes.c_uint64), ("relax_atomics", ctypes.c_uint64),
                 ("entries_scanned", ctypes.c_uint64), ("team_threads", ctypes.c_uint32),
-                ("slots", ctypes.c_uint32), ("bucket_width", ctypes.c_uint64)]
+                ("slots", ctypes.c_uint32), ("bucket_width", ctypes.c_uint64), ("dag_edges", ctypes.c_uint64),
+                ("pair_overflows", ctypes.c_uint64)]
 
 
 class bc_serving_stats(ctypes.Structure):

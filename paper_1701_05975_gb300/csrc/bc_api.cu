@@ -78,6 +78,16 @@ SlabLayout make_layout(uint32_t n, int dist_bits) {
   off += align256((uint64_t)n * 4);
   L.off_far = off;
   off += align256((uint64_t)n * 4);
+  L.off_acc = off;
+  off += align256((uint64_t)n * 8);
+  L.off_pend = off;
+  off += align256(((uint64_t)n + 2) * 4);
+  // DAG edge list: 2 n pairs covers every graph whose shortest-path DAG has at
+  // most two in-edges per vertex on average (sources beyond it fall back to
+  // the per-entry backward scan)
+  L.pair_cap = (uint32_t)std::min<uint64_t>(2ull * n + 64, 0xffffffffull);
+  L.off_pairs = off;
+  off += align256((uint64_t)L.pair_cap * 8);
   L.stride = off;
   return L;
 }
@@ -129,6 +139,11 @@ struct bc_graph {
   uint2* adj = nullptr;
   uint32_t* dnode = nullptr;
   double* ebc = nullptr;  // lazily allocated [nnz]
+  bool relabeled = false;
+  uint32_t* o2n = nullptr;  // device maps (relabeled graphs only)
+  uint32_t* n2o = nullptr;
+  uint32_t* e2o = nullptr;
+  std::vector<uint32_t> h_o2n;  // host copy of old -> new
   uint64_t device_bytes = 0;
   std::string fingerprint;
   TuneCfg tuned;
@@ -150,6 +165,9 @@ GraphDev view(const bc_graph* g) {
   v.row_ptr = g->row_ptr;
   v.adj = g->adj;
   v.dnode = g->dnode;
+  v.o2n = g->o2n;
+  v.n2o = g->n2o;
+  v.e2o = g->e2o;
   return v;
 }
 
@@ -235,8 +253,12 @@ int ws_acquire(bc_graph* g, uint32_t slots, uint32_t k, cudaStream_t st, Workspa
     if (e == cudaSuccess) e = cudaMallocHost(&nw->host_ctl, sizeof(Ctl));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&nw->done, cudaEventDisableTiming);
     // the slab invariant: every distance word is INF between sources
-    // (all-ones bytes everywhere: the other arrays are written before read)
-    if (e == cudaSuccess) e = cudaMemsetAsync(nw->slabs, 0xff, bytes, st);
+    // and the backward accumulators are zero; other arrays are written before read
+    if (e == cudaSuccess)
+      e = launch_fill_slabs(nw->slabs, nw->lay.stride, slots, nw->lay.off_d,
+                            align256((uint64_t)g->n * (g->dist_bits / 8)), 0xffffffffu, st);
+    if (e == cudaSuccess)
+      e = launch_fill_slabs(nw->slabs, nw->lay.stride, slots, nw->lay.off_acc, align256((uint64_t)g->n * 8), 0u, st);
     if (e != cudaSuccess) {
       ws_free(nw.get());
       return cuda_fail(e, "workspace allocation");
@@ -329,6 +351,8 @@ void record_stats(bc_graph* g, const Ctl& c, const RunCfg& r, uint32_t slots) {
   g->last.reached = c.stats[STAT_REACHED];
   g->last.relax_atomics = c.stats[STAT_RELAX];
   g->last.entries_scanned = c.stats[STAT_ENTRIES];
+  g->last.dag_edges = c.stats[STAT_DAG_EDGES];
+  g->last.pair_overflows = c.stats[STAT_PAIR_OVERFLOW];
   g->last.team_threads = r.team;
   g->last.slots = slots;
   g->last.bucket_width = r.width;
@@ -400,8 +424,8 @@ int compute_plain(bc_graph* g, const uint32_t* sources, uint32_t k, double scale
   int dev = DEV_OK;
   unsigned long long stats[STAT_COUNT] = {0};
   if (e == cudaSuccess)
-    e = plain_run(g->plain, view(g), g->dist_bits, sources, k, d_bc, r.width, r.settle_in, r.phase_cap, g->sm_count,
-                  st, &dev, stats);
+    e = plain_run(g->plain, view(g), g->dist_bits, sources, g->relabeled ? g->h_o2n.data() : nullptr, k, d_bc,
+                  r.width, r.settle_in, r.phase_cap, g->sm_count, st, &dev, stats);
   if (e == cudaSuccess && scale != 1.0) e = launch_scale(d_bc, g->n, scale, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(out_bc, d_bc, (size_t)g->n * 8, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -492,6 +516,50 @@ int bc_graph_create(const uint64_t* row_ptr, const uint32_t* col_idx, const uint
     std::sort(b.begin(), b.end());
     if (a != b) return fail(BC_ERR_INVALID, "graph is not symmetric (BC_UNDIRECTED_CHECK)");
   }
+  // Layout: optionally renumber vertices by decreasing degree (stable), so
+  // the per-source state of the vertices most edges point at is contiguous.
+  bool relabel = false;
+  if (flags & BC_RELABEL_DEGREE) {
+    relabel = true;
+  } else if (!(flags & BC_KEEP_ORDER) && n >= 1024) {
+    std::vector<uint64_t> degs(n);
+    for (uint32_t v = 0; v < n; ++v) degs[v] = row_ptr[v + 1] - row_ptr[v];
+    const size_t top = std::max<size_t>(1, n / 100);
+    std::nth_element(degs.begin(), degs.begin() + top, degs.end(), std::greater<uint64_t>());
+    uint64_t top_sum = 0;
+    for (size_t i = 0; i < top; ++i) top_sum += degs[i];
+    relabel = nnz > 0 && (double)top_sum > 0.10 * (double)nnz;
+  }
+  std::vector<uint64_t> rp2;
+  std::vector<uint32_t> col2, w2, n2o, o2n, e2o;
+  if (relabel) {
+    n2o.resize(n);
+    for (uint32_t v = 0; v < n; ++v) n2o[v] = v;
+    std::stable_sort(n2o.begin(), n2o.end(), [&](uint32_t a, uint32_t b) {
+      return row_ptr[a + 1] - row_ptr[a] > row_ptr[b + 1] - row_ptr[b];
+    });
+    o2n.resize(n);
+    for (uint32_t i = 0; i < n; ++i) o2n[n2o[i]] = i;
+    rp2.resize((size_t)n + 1);
+    col2.resize(nnz);
+    w2.resize(nnz);
+    e2o.resize(nnz);
+    rp2[0] = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+      const uint32_t o = n2o[i];
+      const uint64_t deg = row_ptr[o + 1] - row_ptr[o];
+      rp2[i + 1] = rp2[i] + deg;
+      for (uint64_t j = 0; j < deg; ++j) {
+        const uint64_t eo = row_ptr[o] + j, en = rp2[i] + j;
+        col2[en] = o2n[col_idx[eo]];
+        w2[en] = w[eo];
+        e2o[en] = (uint32_t)eo;
+      }
+    }
+    row_ptr = rp2.data();
+    col_idx = col2.data();
+    w = w2.data();
+  }
   auto g = std::make_unique<bc_graph>();
   CK(cudaGetDevice(&g->device));
   CK(cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, g->device));
@@ -516,6 +584,16 @@ int bc_graph_create(const uint64_t* row_ptr, const uint32_t* col_idx, const uint
   if (e == cudaSuccess) e = cudaMemcpyAsync(g->row_ptr, row_ptr, ((size_t)n + 1) * 8, cudaMemcpyHostToDevice, g->stream);
   if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(d_col, col_idx, nnz * 4, cudaMemcpyHostToDevice, g->stream);
   if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(d_w, w, nnz * 4, cudaMemcpyHostToDevice, g->stream);
+  if (e == cudaSuccess && relabel) {
+    g->relabeled = true;
+    e = cudaMalloc(&g->o2n, (size_t)n * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&g->n2o, (size_t)n * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&g->e2o, std::max<size_t>(nnz, 1) * 4);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g->o2n, o2n.data(), (size_t)n * 4, cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g->n2o, n2o.data(), (size_t)n * 4, cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(g->e2o, e2o.data(), nnz * 4, cudaMemcpyHostToDevice, g->stream);
+    g->h_o2n = o2n;
+  }
   if (e == cudaSuccess) e = launch_prep(n, nnz, g->row_ptr, d_col, d_w, g->adj, g->dnode, g->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
   cudaFree(d_col);
@@ -524,10 +602,13 @@ int bc_graph_create(const uint64_t* row_ptr, const uint32_t* col_idx, const uint
     cudaFree(g->row_ptr);
     cudaFree(g->adj);
     cudaFree(g->dnode);
+    cudaFree(g->o2n);
+    cudaFree(g->n2o);
+    cudaFree(g->e2o);
     if (g->stream) cudaStreamDestroy(g->stream);
     return cuda_fail(e, "bc_graph_create upload");
   }
-  g->device_bytes = ((uint64_t)n + 1) * 8 + nnz * 8 + (uint64_t)n * 4;
+  g->device_bytes = ((uint64_t)n + 1) * 8 + nnz * 8 + (uint64_t)n * 4 + (relabel ? 8ull * n + 4ull * nnz : 0);
   *out = g.release();
   return BC_OK;
 }
@@ -547,6 +628,9 @@ int bc_graph_destroy(bc_graph_t g) {
   cudaFree(g->adj);
   cudaFree(g->dnode);
   cudaFree(g->ebc);
+  cudaFree(g->o2n);
+  cudaFree(g->n2o);
+  cudaFree(g->e2o);
   cudaStreamDestroy(g->stream);
   delete g;
   return BC_OK;
@@ -616,6 +700,18 @@ int bc_sync_status(bc_graph_t g, void* stream) {
     if (it != g->async_ws.end()) w = it->second;
   }
   if (!w) return BC_OK;
+  {
+    std::lock_guard<std::mutex> lk(g->mu);
+    const Ctl& c = *w->host_ctl;
+    g->last.sources = c.stats[STAT_SOURCES];
+    g->last.phases = c.stats[STAT_PHASES];
+    g->last.refills = c.stats[STAT_REFILLS];
+    g->last.reached = c.stats[STAT_REACHED];
+    g->last.relax_atomics = c.stats[STAT_RELAX];
+    g->last.entries_scanned = c.stats[STAT_ENTRIES];
+    g->last.dag_edges = c.stats[STAT_DAG_EDGES];
+    g->last.pair_overflows = c.stats[STAT_PAIR_OVERFLOW];
+  }
   return status_from_dev(w->host_ctl->err);
 }
 
@@ -643,7 +739,7 @@ int bc_sssp_debug(bc_graph_t g, uint32_t s, uint64_t* out_dist, double* out_sigm
   Workspace* w = nullptr;
   int rc = ws_acquire(g, 1, 1, st, &w);
   if (rc) return rc;
-  w->host_src[0] = s;
+  w->host_src[0] = s;  // the kernel maps caller ids to internal ids
   const uint32_t n = g->n;
   std::vector<uint8_t> dbuf((size_t)n * (g->dist_bits / 8));
   std::vector<double> sig(n);
@@ -676,15 +772,16 @@ int bc_sssp_debug(bc_graph_t g, uint32_t s, uint64_t* out_dist, double* out_sigm
   std::vector<uint32_t> level(n, 0xffffffffu);
   for (uint32_t l = 0; l < nlev; ++l)
     for (uint32_t i = ends[l]; i < ends[l + 1] && i < reached; ++i) level[S[i]] = l;
-  for (uint32_t v = 0; v < n; ++v) {
+  for (uint32_t ov = 0; ov < n; ++ov) {
+    const uint32_t v = g->relabeled ? g->h_o2n[ov] : ov;  // internal id
     const bool reached_v = level[v] != 0xffffffffu;
     if (out_dist) {
-      if (!reached_v) out_dist[v] = UINT64_MAX;
-      else if (g->dist_bits == 32) out_dist[v] = reinterpret_cast<const uint32_t*>(dbuf.data())[v];
-      else out_dist[v] = reinterpret_cast<const uint64_t*>(dbuf.data())[v];
+      if (!reached_v) out_dist[ov] = UINT64_MAX;
+      else if (g->dist_bits == 32) out_dist[ov] = reinterpret_cast<const uint32_t*>(dbuf.data())[v];
+      else out_dist[ov] = reinterpret_cast<const uint64_t*>(dbuf.data())[v];
     }
-    if (out_sigma) out_sigma[v] = reached_v ? sig[v] : 0.0;
-    if (out_level) out_level[v] = level[v];
+    if (out_sigma) out_sigma[ov] = reached_v ? sig[v] : 0.0;
+    if (out_level) out_level[ov] = level[v];
   }
   return BC_OK;
 }

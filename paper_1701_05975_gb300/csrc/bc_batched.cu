@@ -33,6 +33,8 @@ namespace bcgpu {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
+constexpr uint32_t NONE = 0xffffffffu;
+constexpr int UNROLL = 4;  // independent edge loads in flight per thread
 
 template <typename D>
 __device__ __forceinline__ D dinf() {
@@ -72,6 +74,7 @@ template <typename D, int TEAM>
 struct TeamShared {
   uint32_t src_idx;
   uint32_t near_len, far_len, S_len, nlev;
+  uint32_t pair_len, pair_over;
   int stop;
   D split;
   uint32_t off[TEAM + 1];
@@ -174,6 +177,10 @@ struct Slab {
   uint32_t* ends;
   uint32_t* nearq;
   uint32_t* farq;
+  double* bacc;     // backward accumulator: sum of successor coefficients
+  uint32_t* pend;   // pend[l] = end of level l's DAG edges in pairs
+  uint2* pairs;     // DAG edges {predecessor u, vertex v}
+  uint32_t pair_cap;
 };
 
 template <typename D>
@@ -186,6 +193,10 @@ __device__ __forceinline__ Slab<D> slab_at(const BatchArgs& a, uint32_t slot) {
   s.ends = reinterpret_cast<uint32_t*>(base + a.lay.off_ends);
   s.nearq = reinterpret_cast<uint32_t*>(base + a.lay.off_near);
   s.farq = reinterpret_cast<uint32_t*>(base + a.lay.off_far);
+  s.bacc = reinterpret_cast<double*>(base + a.lay.off_acc);
+  s.pend = reinterpret_cast<uint32_t*>(base + a.lay.off_pend);
+  s.pairs = reinterpret_cast<uint2*>(base + a.lay.off_pairs);
+  s.pair_cap = a.lay.pair_cap;
   return s;
 }
 
@@ -235,30 +246,54 @@ __device__ void expand_forward(const BatchArgs& a, const Slab<D>& sl, TeamShared
     const uint32_t cnt = min((uint32_t)TEAM, f1 - base);
     const uint32_t total = load_chunk<D, TEAM>(a, sl, sh, base, cnt, t, false);
     scanned += (t == 0) ? total : 0;
-    for (uint32_t e = t; e < total; e += TEAM) {
-      const uint32_t i = owner_of<TEAM>(sh.off, cnt, e);
-      const uint2 ent = __ldg(&a.g.adj[sh.rs[i] + (e - sh.off[i])]);
-      const uint32_t u = ent.x;
-      const D w = (D)ent.y;
-      const D dvi = sh.dv[i];
-      const D du = ldcg(&sl.d[u]);
-      if (du != INF && du + w == dvi) {
-        // u is a shortest-path predecessor of v (settled in an earlier batch)
-        atomicAdd(&sh.acc[i], ldcg(&sl.sig[u]));
-      } else {
-        const D nd = dvi + w;
-        if (nd < du) {
-          ++relax;
-          const D old = atomic_min_d(&sl.d[u], nd);
-          if (nd < old) {
-            if (old == INF) {
-              if (nd < split) {
+    // ILP: each thread first issues UNROLL independent adjacency loads, then
+    // UNROLL independent distance gathers, then processes them
+    for (uint32_t e0 = t; e0 < total; e0 += TEAM * UNROLL) {
+      uint32_t iv[UNROLL];
+      uint2 ent[UNROLL];
+#pragma unroll
+      for (int q = 0; q < UNROLL; ++q) {
+        const uint32_t e = e0 + q * TEAM;
+        iv[q] = NONE;
+        ent[q] = make_uint2(0, 0);
+        if (e < total) {
+          iv[q] = owner_of<TEAM>(sh.off, cnt, e);
+          ent[q] = __ldg(&a.g.adj[sh.rs[iv[q]] + (e - sh.off[iv[q]])]);
+        }
+      }
+      D dus[UNROLL];
+#pragma unroll
+      for (int q = 0; q < UNROLL; ++q) dus[q] = (iv[q] != NONE) ? ldcg(&sl.d[ent[q].x]) : INF;
+#pragma unroll
+      for (int q = 0; q < UNROLL; ++q) {
+        if (iv[q] == NONE) continue;
+        const uint32_t i = iv[q];
+        const uint32_t u = ent[q].x;
+        const D w = (D)ent[q].y;
+        const D dvi = sh.dv[i];
+        const D du = dus[q];
+        if (du != INF && du + w == dvi) {
+          // u is a shortest-path predecessor of v (settled in an earlier
+          // batch): pull its sigma and record the DAG edge u -> v
+          atomicAdd(&sh.acc[i], ldcg(&sl.sig[u]));
+          const uint32_t pos = atomicAdd(&sh.pair_len, 1u);
+          if (pos < sl.pair_cap) sl.pairs[pos] = make_uint2(u, sh.vtx[i]);
+          else sh.pair_over = 1;
+        } else {
+          const D nd = dvi + w;
+          if (nd < du) {
+            ++relax;
+            const D old = atomic_min_d(&sl.d[u], nd);
+            if (nd < old) {
+              if (old == INF) {
+                if (nd < split) {
+                  sl.nearq[atomicAdd(&sh.near_len, 1u)] = u;
+                } else {
+                  sl.farq[atomicAdd(&sh.far_len, 1u)] = u;
+                }
+              } else if (old >= split && nd < split) {
                 sl.nearq[atomicAdd(&sh.near_len, 1u)] = u;
-              } else {
-                sl.farq[atomicAdd(&sh.far_len, 1u)] = u;
               }
-            } else if (old >= split && nd < split) {
-              sl.nearq[atomicAdd(&sh.near_len, 1u)] = u;
             }
           }
         }
@@ -280,17 +315,36 @@ __device__ void accumulate_level(const BatchArgs& a, const Slab<D>& sl, TeamShar
     const uint32_t cnt = min((uint32_t)TEAM, f1 - base);
     const uint32_t total = load_chunk<D, TEAM>(a, sl, sh, base, cnt, t, edges);
     scanned += (t == 0) ? total : 0;
-    for (uint32_t e = t; e < total; e += TEAM) {
-      const uint32_t i = owner_of<TEAM>(sh.off, cnt, e);
-      const uint64_t entry = sh.rs[i] + (e - sh.off[i]);
-      const uint2 ent = __ldg(&a.g.adj[entry]);
-      const uint32_t u = ent.x;
-      const D du = ldcg(&sl.d[u]);
-      if (du != INF && du == sh.dv[i] + (D)ent.y) {
-        // u is a successor: its coefficient c(u) is final (later level)
-        const double cu = ldcg(&sl.sig[u]);
-        atomicAdd(&sh.acc[i], cu);
-        if (edges) atomicAdd(&a.ebc[entry], sh.sv[i] * cu);
+    for (uint32_t e0 = t; e0 < total; e0 += TEAM * UNROLL) {
+      uint32_t iv[UNROLL];
+      uint64_t entry[UNROLL];
+      uint2 ent[UNROLL];
+#pragma unroll
+      for (int q = 0; q < UNROLL; ++q) {
+        const uint32_t e = e0 + q * TEAM;
+        iv[q] = NONE;
+        entry[q] = 0;
+        ent[q] = make_uint2(0, 0);
+        if (e < total) {
+          iv[q] = owner_of<TEAM>(sh.off, cnt, e);
+          entry[q] = sh.rs[iv[q]] + (e - sh.off[iv[q]]);
+          ent[q] = __ldg(&a.g.adj[entry[q]]);
+        }
+      }
+      D dus[UNROLL];
+#pragma unroll
+      for (int q = 0; q < UNROLL; ++q) dus[q] = (iv[q] != NONE) ? ldcg(&sl.d[ent[q].x]) : INF;
+#pragma unroll
+      for (int q = 0; q < UNROLL; ++q) {
+        if (iv[q] == NONE) continue;
+        const uint32_t i = iv[q];
+        const D du = dus[q];
+        if (du != INF && du == sh.dv[i] + (D)ent[q].y) {
+          // ent.x is a successor: its coefficient c is final (later level)
+          const double cu = ldcg(&sl.sig[ent[q].x]);
+          atomicAdd(&sh.acc[i], cu);
+          if (edges) atomicAdd(&a.ebc[a.g.e2o ? __ldg(&a.g.e2o[entry[q]]) : entry[q]], sh.sv[i] * cu);
+        }
       }
     }
     team_sync<TEAM>();
@@ -299,9 +353,46 @@ __device__ void accumulate_level(const BatchArgs& a, const Slab<D>& sl, TeamShar
       const double sg = ldcg(&sl.sig[v]);
       const double delta = sg * sh.acc[t];
       sl.sig[v] = (1.0 + delta) / sg;
-      if (v != s) atomicAdd(&a.bc[v], delta);
+      if (v != s) atomicAdd(&a.bc[a.g.n2o ? __ldg(&a.g.n2o[v]) : v], delta);
     }
     team_sync<TEAM>();
+  }
+}
+
+// Backward step 1 for one level: every successor has pushed its coefficient
+// into bacc, so delta(v) = sigma(v) * bacc(v) is final; store
+// c(v) = (1 + delta(v)) / sigma(v) in sigma's slot and add delta(v) to BC.
+template <typename D, int TEAM>
+__device__ __forceinline__ void finalize_level(const BatchArgs& a, const Slab<D>& sl, uint32_t b0, uint32_t b1,
+                                               int t) {
+  for (uint32_t j = b0 + t; j < b1; j += TEAM) {
+    const uint32_t v = ldcg(&sl.S[j]);
+    const double acc = ldcg(&sl.bacc[v]);
+    const double sg = ldcg(&sl.sig[v]);
+    const double delta = sg * acc;
+    sl.sig[v] = (1.0 + delta) / sg;
+    if (acc != 0.0) {
+      sl.bacc[v] = 0.0;
+      atomicAdd(&a.bc[a.g.n2o ? __ldg(&a.g.n2o[v]) : v], delta);
+    }
+  }
+}
+
+// Backward step 2 for one level: each DAG edge u -> v into the level adds
+// c(v) to bacc(u) (FP64 atomics; u lies in an earlier level).
+template <int TEAM>
+__device__ __forceinline__ void push_level_pairs(const uint2* pairs, double* bacc, const double* sig, uint32_t p0,
+                                                 uint32_t p1, int t) {
+  for (uint32_t p = p0 + t; p < p1; p += TEAM * UNROLL) {
+    uint2 pr[UNROLL];
+#pragma unroll
+    for (int q = 0; q < UNROLL; ++q) pr[q] = (p + q * TEAM < p1) ? __ldcg(&pairs[p + q * TEAM]) : make_uint2(NONE, 0);
+    double c[UNROLL];
+#pragma unroll
+    for (int q = 0; q < UNROLL; ++q) c[q] = (pr[q].x != NONE) ? __ldcg(&sig[pr[q].y]) : 0.0;
+#pragma unroll
+    for (int q = 0; q < UNROLL; ++q)
+      if (pr[q].x != NONE) atomicAdd(&bacc[pr[q].x], c[q]);
   }
 }
 
@@ -322,6 +413,8 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
     sh.far_len = 0;
     sh.S_len = 1;
     sh.nlev = 1;
+    sh.pair_len = 0;
+    sh.pair_over = 0;
     sh.stop = 0;
     sh.split = sat_add<D>((D)0, a.width);
   }
@@ -330,6 +423,8 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
   for (;;) {
     const D split0 = sh.split;
     expand_forward<D, TEAM>(a, sl, sh, f0, f1, s, t, split0, relax, scanned);
+    // DAG edges into the batch just expanded end here
+    if (t == 0) sl.pend[sh.nlev - 1] = sh.pair_len;
     // refill the near queue from the far queue when it runs dry
     while (sh.near_len == 0 && sh.far_len > 0) {
       const D old = sh.split;
@@ -440,14 +535,26 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
       a.debug_out[1] = sh.S_len;
     }
   } else {
-    // level 0 is the source: delta(s) is not part of BC, but with edge
-    // output its outgoing shortest-path edges still carry shares
     const uint32_t nlev = sh.nlev;
-    const int last = a.ebc ? 0 : 1;
-    for (int lev = (int)nlev - 1; lev >= last; --lev) {
-      const uint32_t b0 = ldcg(&sl.ends[lev]);
-      const uint32_t b1 = ldcg(&sl.ends[lev + 1]);
-      accumulate_level<D, TEAM>(a, sl, sh, b0, b1, s, t, scanned);
+    if (!a.ebc && !sh.pair_over) {
+      // Algorithm 3 over the recorded DAG edges: levels in reverse; finalize
+      // the level's vertices, then push their coefficients to predecessors
+      for (int lev = (int)nlev - 1; lev >= 1; --lev) {
+        finalize_level<D, TEAM>(a, sl, ldcg(&sl.ends[lev]), ldcg(&sl.ends[lev + 1]), t);
+        team_sync<TEAM>();
+        push_level_pairs<TEAM>(sl.pairs, sl.bacc, sl.sig, ldcg(&sl.pend[lev - 1]), ldcg(&sl.pend[lev]), t);
+        team_sync<TEAM>();
+      }
+      if (t == 0) sl.bacc[s] = 0.0;  // the source collected shares it does not keep
+    } else {
+      // per-entry scan: level 0 is the source; delta(s) is not part of BC,
+      // but with edge output its outgoing shortest-path edges carry shares
+      const int last = a.ebc ? 0 : 1;
+      for (int lev = (int)nlev - 1; lev >= last; --lev) {
+        const uint32_t b0 = ldcg(&sl.ends[lev]);
+        const uint32_t b1 = ldcg(&sl.ends[lev + 1]);
+        accumulate_level<D, TEAM>(a, sl, sh, b0, b1, s, t, scanned);
+      }
     }
     // restore the slab invariant: d = INF on every vertex this source reached
     const uint32_t n_reached = sh.S_len;
@@ -464,6 +571,8 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
       atomicAdd(&a.stats[STAT_REFILLS], (unsigned long long)refills);
       atomicAdd(&a.stats[STAT_REACHED], (unsigned long long)sh.S_len);
       atomicAdd(&a.stats[STAT_ENTRIES], scanned);
+      atomicAdd(&a.stats[STAT_DAG_EDGES], (unsigned long long)sh.pair_len);
+      atomicAdd(&a.stats[STAT_PAIR_OVERFLOW], (unsigned long long)sh.pair_over);
     }
   }
   team_sync<TEAM>();
@@ -488,11 +597,12 @@ __global__ void __launch_bounds__(BLOCK) bc_batched_kernel(const BatchArgs a) {
     const uint32_t idx = sh.src_idx;
     team_sync<TEAM>();
     if (idx >= a.k) break;
-    const uint32_t s = __ldg(&a.sources[idx]);
+    uint32_t s = __ldg(&a.sources[idx]);
     if (s >= a.g.n) {
       if (t == 0) atomicCAS(a.err, DEV_OK, DEV_ERR_INVALID);
       continue;
     }
+    if (a.g.o2n) s = __ldg(&a.g.o2n[s]);
     const bool ok = run_source<D, TEAM>(a, sl, sh, s, t);
     if (!ok || (a.flags & RUN_FORWARD_ONLY)) break;
   }

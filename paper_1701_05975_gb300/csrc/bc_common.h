@@ -16,6 +16,13 @@ struct GraphDev {
   const uint64_t* row_ptr;  // [n + 1]
   const uint2* adj;         // [nnz] {neighbour, weight}
   const uint32_t* dnode;    // [n] Delta_node(v) = min incident weight (UINT32_MAX if isolated)
+  // Optional relabeling (graph prep orders vertices by decreasing degree so
+  // the state of high-degree vertices is contiguous).  Internal ids are
+  // "new"; the caller's ids are "old".  All three are nullptr when the graph
+  // keeps the caller's order.
+  const uint32_t* o2n;      // [n] old id -> new id (applied to sources)
+  const uint32_t* n2o;      // [n] new id -> old id (applied to BC output)
+  const uint32_t* e2o;      // [nnz] new CSR entry -> old CSR entry (edge BC output)
 };
 
 // Byte offsets of the per-source arrays inside one slab (one slab per source
@@ -24,9 +31,15 @@ struct GraphDev {
 // pass, S: settle order (the level lists of Algorithm 1's S/ends), ends: level
 // boundaries, nearq / farq: candidate queues (reached, unsettled vertices
 // below / at or above the current split).
+// acc: per-vertex sum of successor coefficients during the backward pass
+// (zero between sources); pend: end of each level's range in the DAG edge
+// list; pairs: the shortest-path DAG edges (u -> v) found while pulling sigma,
+// in level order of v (capacity pair_cap; on overflow the backward pass falls
+// back to scanning every CSR entry).
 struct SlabLayout {
   uint64_t stride;
-  uint64_t off_d, off_sig, off_S, off_ends, off_near, off_far;
+  uint64_t off_d, off_sig, off_S, off_ends, off_near, off_far, off_acc, off_pend, off_pairs;
+  uint32_t pair_cap;
 };
 
 enum : uint32_t {
@@ -47,6 +60,8 @@ enum : int {
   STAT_REACHED,
   STAT_RELAX,
   STAT_ENTRIES,
+  STAT_DAG_EDGES,
+  STAT_PAIR_OVERFLOW,
   STAT_COUNT
 };
 
@@ -80,6 +95,9 @@ cudaError_t launch_prep(uint32_t n, uint64_t nnz, const uint64_t* row_ptr, const
 cudaError_t launch_fill_u64(uint64_t* p, uint64_t count, uint64_t value, cudaStream_t st);
 cudaError_t launch_scale(double* p, uint64_t count, double scale, cudaStream_t st);
 cudaError_t launch_check_sources(const uint32_t* src, uint32_t k, uint32_t n, int* err, cudaStream_t st);
+// Fill `bytes` (a multiple of 4) at offset `off` of every slot of a slab array.
+cudaError_t launch_fill_slabs(char* base, uint64_t stride, uint32_t nslots, uint64_t off, uint64_t bytes,
+                              uint32_t value, cudaStream_t st);
 
 // Plain form (bc_plain.cu): one source at a time over the whole GPU.
 struct PlainWork;
@@ -88,8 +106,10 @@ void plain_destroy(PlainWork* w);
 uint64_t plain_bytes(uint32_t n, int dist_bits);
 // Runs sources[0..k) (HOST list) one after another; adds raw delta into bc.
 // Returns DEV_* status through *dev_status.
-cudaError_t plain_run(PlainWork* w, const GraphDev& g, int dist_bits, const uint32_t* host_sources, uint32_t k,
-                      double* bc, uint64_t width, uint32_t settle_in, uint64_t phase_cap, int sm_count,
-                      cudaStream_t st, int* dev_status, unsigned long long* host_stats);
+// host_o2n: the graph's old -> new id map on the host (nullptr: no relabeling).
+cudaError_t plain_run(PlainWork* w, const GraphDev& g, int dist_bits, const uint32_t* host_sources,
+                      const uint32_t* host_o2n, uint32_t k, double* bc, uint64_t width, uint32_t settle_in,
+                      uint64_t phase_cap, int sm_count, cudaStream_t st, int* dev_status,
+                      unsigned long long* host_stats);
 
 }  // namespace bcgpu

@@ -219,7 +219,7 @@ __global__ void backward_kernel(GraphDev g, const D* d, double* sig, const uint3
       const double sg = sig[v];
       const double delta = sg * acc;
       sig[v] = (1.0 + delta) / sg;
-      atomicAdd(&bc[v], delta);
+      atomicAdd(&bc[g.n2o ? g.n2o[v] : v], delta);
     }
   }
 }
@@ -248,18 +248,18 @@ inline int blocks_for(uint64_t items, int per_block, int cap) {
   } while (0)
 
 template <typename D>
-cudaError_t run_t(PlainWork* w, const GraphDev& g, const uint32_t* src, uint32_t k, double* bc, uint64_t width,
-                  uint32_t settle_in, uint64_t phase_cap, int sm_count, cudaStream_t st, int* dev_status,
-                  unsigned long long* stats) {
+cudaError_t run_t(PlainWork* w, const GraphDev& g, const uint32_t* src, const uint32_t* host_o2n, uint32_t k,
+                  double* bc, uint64_t width, uint32_t settle_in, uint64_t phase_cap, int sm_count, cudaStream_t st,
+                  int* dev_status, unsigned long long* stats) {
   D* d = static_cast<D*>(w->d);
   const int cap = sm_count * 8;
   *dev_status = DEV_OK;
   for (uint32_t i = 0; i < k; ++i) {
-    const uint32_t s = src[i];
-    if (s >= g.n) {
+    if (src[i] >= g.n) {
       *dev_status = DEV_ERR_INVALID;
       return cudaSuccess;
     }
+    const uint32_t s = host_o2n ? host_o2n[src[i]] : src[i];
     int cn = 0, cf = 0;  // current near / far buffers
     init_kernel<D><<<1, 1, 0, st>>>(d, w->sig, w->S, w->ctr, s, width);
     PCHK(cudaGetLastError());
@@ -377,14 +377,15 @@ void plain_destroy(PlainWork* w) {
   delete w;
 }
 
-cudaError_t plain_run(PlainWork* w, const GraphDev& g, int dist_bits, const uint32_t* host_sources, uint32_t k,
-                      double* bc, uint64_t width, uint32_t settle_in, uint64_t phase_cap, int sm_count,
-                      cudaStream_t st, int* dev_status, unsigned long long* host_stats) {
+cudaError_t plain_run(PlainWork* w, const GraphDev& g, int dist_bits, const uint32_t* host_sources,
+                      const uint32_t* host_o2n, uint32_t k, double* bc, uint64_t width, uint32_t settle_in,
+                      uint64_t phase_cap, int sm_count, cudaStream_t st, int* dev_status,
+                      unsigned long long* host_stats) {
   if (dist_bits == 32)
-    return run_t<uint32_t>(w, g, host_sources, k, bc, width, settle_in, phase_cap, sm_count, st, dev_status,
-                           host_stats);
-  return run_t<uint64_t>(w, g, host_sources, k, bc, width, settle_in, phase_cap, sm_count, st, dev_status,
-                         host_stats);
+    return run_t<uint32_t>(w, g, host_sources, host_o2n, k, bc, width, settle_in, phase_cap, sm_count, st,
+                           dev_status, host_stats);
+  return run_t<uint64_t>(w, g, host_sources, host_o2n, k, bc, width, settle_in, phase_cap, sm_count, st,
+                         dev_status, host_stats);
 }
 
 }  // namespace bcgpu

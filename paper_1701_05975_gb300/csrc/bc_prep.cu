@@ -6,6 +6,7 @@
 // per vertex.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "bc_common.h"
@@ -48,6 +49,15 @@ __global__ void check_sources_kernel(const uint32_t* src, uint32_t k, uint32_t n
     if (src[i] >= n) atomicCAS(err, DEV_OK, DEV_ERR_INVALID);
 }
 
+__global__ void fill_slabs_kernel(char* base, uint64_t stride, uint32_t nslots, uint64_t off, uint64_t words,
+                                  uint32_t value) {
+  for (uint32_t slot = blockIdx.y; slot < nslots; slot += gridDim.y) {
+    uint32_t* p = reinterpret_cast<uint32_t*>(base + (uint64_t)slot * stride + off);
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < words; i += (uint64_t)gridDim.x * blockDim.x)
+      p[i] = value;
+  }
+}
+
 int grid_for(uint64_t work, int block) {
   uint64_t g = (work + block - 1) / block;
   if (g < 1) g = 1;
@@ -79,6 +89,15 @@ cudaError_t launch_scale(double* p, uint64_t count, double scale, cudaStream_t s
 cudaError_t launch_check_sources(const uint32_t* src, uint32_t k, uint32_t n, int* err, cudaStream_t st) {
   if (k == 0) return cudaSuccess;
   check_sources_kernel<<<grid_for(k, 256), 256, 0, st>>>(src, k, n, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_slabs(char* base, uint64_t stride, uint32_t nslots, uint64_t off, uint64_t bytes,
+                              uint32_t value, cudaStream_t st) {
+  if (nslots == 0 || bytes == 0) return cudaSuccess;
+  const uint64_t words = bytes / 4;
+  dim3 grid((unsigned)std::min<uint64_t>((words + 255) / 256, 64), std::min<uint32_t>(nslots, 65535));
+  fill_slabs_kernel<<<grid, 256, 0, st>>>(base, stride, nslots, off, words, value);
   return cudaGetLastError();
 }
 

@@ -201,3 +201,48 @@ def test_async_with_torch_buffers():
         with pytest.raises(bc.BCError) as ei:
             bc.bc_sync_status(G.handle, stream.cuda_stream)
         assert ei.value.code == bc.BC_ERR_INVALID
+
+
+@pytest.mark.parametrize("flags", [bc.BC_RELABEL_DEGREE, bc.BC_KEEP_ORDER])
+def test_relabeled_and_kept_layouts_agree_with_oracle(flags):
+    rng = np.random.default_rng(77)
+    for i in range(12):
+        g = gen.ba_graph(int(rng.integers(6, 300)), int(rng.integers(1, 4)), 1, int(rng.choice([2, 40])), seed=i)
+        src = np.arange(g.n, dtype=np.uint32)
+        with bc.Graph(g, flags=flags) as G:
+            assert_bc_close(G.compute(src, 0.5), oracle.bc(g, src, 0.5))
+            ebc, _ = G.edge_compute(src[::3], 1.0)
+            assert_bc_close(ebc, oracle.edge_bc(g, src[::3], 1.0))
+            s = int(rng.integers(0, g.n))
+            d, sg, lev = G.sssp_debug(s)
+            d_ref, sg_ref, _ = oracle.sssp(g, s)
+            assert np.array_equal(d, d_ref) and np.array_equal(sg, sg_ref)
+    g = gen.er_graph(300, 1000, 1, 9, seed=3)
+    bc.bc_set_config(mode=bc.BC_MODE_PLAIN)
+    with bc.Graph(g, flags=flags) as G:
+        assert_bc_close(G.compute(np.arange(0, 300, 11, dtype=np.uint32), 1.0),
+                        oracle.bc(g, np.arange(0, 300, 11, dtype=np.uint32), 1.0))
+
+
+def test_dag_edge_list_overflow_falls_back_to_entry_scan():
+    # layers of 20 vertices, complete bipartite between consecutive layers,
+    # unit weights: every vertex beyond the first layer has 20 predecessors,
+    # far more DAG edges than the per-source list holds (2 n + 64)
+    L, layers = 20, 5
+    edges = [(a * L + i, (a + 1) * L + j, 1) for a in range(layers - 1) for i in range(L) for j in range(L)]
+    g = graph(L * layers, edges)
+    src = np.arange(g.n, dtype=np.uint32)
+    for team in (32, 256):
+        bc.bc_set_config(team_threads=team)
+        with bc.Graph(g) as G:
+            assert_bc_close(G.compute(src, 0.5), oracle.bc(g, src, 0.5))
+            st = G.stats()
+            assert st.pair_overflows > 0
+            d, sg, _ = G.sssp_debug(0)
+            d_ref, sg_ref, _ = oracle.sssp(g, 0)
+            assert np.array_equal(d, d_ref) and np.array_equal(sg, sg_ref)
+    g2 = gen.er_graph(500, 3000, 1, 1000, seed=2)
+    with bc.Graph(g2) as G:
+        G.compute(np.arange(500, dtype=np.uint32), 1.0)
+        st = G.stats()
+        assert st.pair_overflows == 0 and st.dag_edges >= 499 * 500 * 0.9
