@@ -237,6 +237,39 @@ int bc_last_run_stats(bc_graph_t g, bc_run_stats *out);
  */
 int bc_autotune(bc_graph_t g, const uint32_t *sources, uint32_t k_probe);
 
+/*
+ * No-allocation variant of bc_compute_async, for callers that cannot allocate
+ * device memory while they run (a host thread with real-time limits, code
+ * running while another framework owns the device allocator, a process whose
+ * memory is reserved up front).  The paper has no counterpart: it is an
+ * interface addition.
+ *
+ * Inputs and outputs are the caller's DEVICE arrays: the CSR of the
+ * undirected graph (d_row_ptr[n + 1], d_col_idx[nnz], d_w[nnz], the same
+ * conventions as bc_graph_create; the contents are validated on the device),
+ * d_sources[k], d_out_bc[n] (overwritten with scale * sum_s delta_s, in the
+ * caller's vertex ids) and d_status (one int, set to BC_OK, BC_ERR_INVALID or
+ * BC_ERR_TIMEOUT when the work completes).  Work is enqueued on `stream`
+ * (a cudaStream_t) and the call returns without waiting.
+ *
+ * All scratch lives in one fixed device array of BC_NOALLOC_SCRATCH_BYTES
+ * that every GPU loading this library holds until the process exits; the call
+ * makes no cudaMalloc or cudaFree and calls no allocating routine.  A graph
+ * whose packed CSR, per-vertex data and one per-source slab do not fit is
+ * rejected with BC_ERR_NOMEM before any device work; fewer sources then run
+ * at once when only a few slabs fit.  Distances use 64-bit words.
+ *
+ * The first call on a device looks up the array's device address, so make it
+ * before any stream capture.  Calls share the array and each re-initialises
+ * it; calls whose work overlaps on the GPU (other streams or threads without
+ * ordering) race on it.  Tuning fields of bc_config (bucket_width, settle_in,
+ * phase_cap) apply.
+ */
+#define BC_NOALLOC_SCRATCH_BYTES (64ull << 20)
+int bc_compute_noalloc(const uint64_t *d_row_ptr, const uint32_t *d_col_idx, const uint32_t *d_w, uint32_t n,
+                       uint64_t nnz, const uint32_t *d_sources, uint32_t k, double scale, double *d_out_bc,
+                       int *d_status, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -93,6 +93,7 @@ _SIGNATURES = {
     "bc_sssp_debug": [_vp, _u32, _vp, _vp, _vp],
     "bc_last_run_stats": [_vp, ctypes.POINTER(bc_run_stats)],
     "bc_autotune": [_vp, _vp, _u32],
+    "bc_compute_noalloc": [_vp, _vp, _vp, _u32, _u64, _vp, _u32, _f64, _vp, _vp, _vp],
 }
 
 _lib = None
@@ -237,6 +238,14 @@ def bc_last_run_stats(h) -> bc_run_stats:
 def bc_autotune(h, sources):
     src = np.ascontiguousarray(sources, dtype=np.uint32)
     _check(lib().bc_autotune(h, _ptr(src), len(src)))
+
+
+def bc_compute_noalloc(d_row_ptr: int, d_col_idx: int, d_w: int, n: int, nnz: int, d_sources: int, k: int,
+                       scale: float, d_out_bc: int, d_status: int, stream_ptr: int):
+    """All pointers are device addresses owned by the caller (see bcgpu.h)."""
+    _check(lib().bc_compute_noalloc(ctypes.c_void_p(d_row_ptr), ctypes.c_void_p(d_col_idx), ctypes.c_void_p(d_w), n,
+                                    nnz, ctypes.c_void_p(d_sources), k, scale, ctypes.c_void_p(d_out_bc),
+                                    ctypes.c_void_p(d_status), ctypes.c_void_p(stream_ptr)))
 
 
 # ------------------------------------------------------------ convenience

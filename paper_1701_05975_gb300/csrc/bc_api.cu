@@ -459,6 +459,8 @@ std::string fingerprint(uint32_t n, uint64_t nnz, const uint64_t* rp, const uint
 
 }  // namespace
 
+int bcgpu::set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
 // ===================================================================== ABI
 
 extern "C" {

@@ -99,6 +99,9 @@ cudaError_t launch_check_sources(const uint32_t* src, uint32_t k, uint32_t n, in
 cudaError_t launch_fill_slabs(char* base, uint64_t stride, uint32_t nslots, uint64_t off, uint64_t bytes,
                               uint32_t value, cudaStream_t st);
 
+// Record a message for bc_last_error() on the calling thread; returns code.
+int set_error(int code, const char* msg);
+
 // Plain form (bc_plain.cu): one source at a time over the whole GPU.
 struct PlainWork;
 PlainWork* plain_create(uint32_t n, int dist_bits, cudaError_t* e);
