@@ -200,8 +200,10 @@ RunCfg resolve(const bc_graph* g) {
   RunCfg r;
   r.mode = c.mode;
   const double avg_deg = g->n ? (double)g->nnz / g->n : 0.0;
-  r.team = c.team_threads ? c.team_threads
-                          : (g->tuned.team ? g->tuned.team : ((avg_deg <= 12.0 || g->n <= 8192) ? 32u : 256u));
+  // measured defaults: wide CTA teams for dense skewed graphs (large
+  // frontiers per batch), 128-thread teams for sparse high-diameter graphs
+  const uint32_t team_default = avg_deg >= 20.0 ? 512u : (avg_deg >= 6.0 ? 256u : 128u);
+  r.team = c.team_threads ? c.team_threads : (g->tuned.team ? g->tuned.team : team_default);
   r.width = c.bucket_width ? c.bucket_width
                            : (g->tuned.width ? g->tuned.width : std::max<uint64_t>(1, g->max_w / 4));
   uint32_t si = c.settle_in ? c.settle_in : (g->tuned.settle_in ? g->tuned.settle_in : 1u);
@@ -460,6 +462,86 @@ std::string fingerprint(uint32_t n, uint64_t nnz, const uint64_t* rp, const uint
 }  // namespace
 
 int bcgpu::set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
+// ------------------------------------------------------------- serving glue
+
+struct bcgpu::ServeLease {
+  bc_graph* g;
+  Workspace* w;
+  cudaStream_t st;
+  cudaEvent_t ev;
+  uint32_t k;
+};
+
+int bcgpu::graph_device(const bc_graph* g) { return g->device; }
+uint32_t bcgpu::graph_n(const bc_graph* g) { return g->n; }
+uint64_t bcgpu::graph_nnz(const bc_graph* g) { return g->nnz; }
+void bcgpu::graph_serving_ref(bc_graph* g, int delta) { g->serving_refs += delta; }
+
+int bcgpu::serve_plan(bc_graph* g, ServePlan* out) {
+  RunCfg r = resolve(g);
+  int bps = 0;
+  cudaError_t e = batched_occupancy(g->dist_bits, (int)r.team, &bps);
+  if (e != cudaSuccess) return cuda_fail(e, "occupancy");
+  const uint32_t per_block = (uint32_t)(batched_block_threads((int)r.team) / (int)r.team);
+  out->team = r.team;
+  out->max_slots = (uint32_t)std::max(bps, 1) * (uint32_t)g->sm_count * per_block;
+  out->slot_bytes = make_layout(g->n, g->dist_bits).stride;
+  out->fixed_bytes = (uint64_t)g->n * 16 + 4096;
+  return BC_OK;
+}
+
+int bcgpu::serve_start(bc_graph* g, const uint32_t* sources, uint32_t k, double scale, uint32_t slots,
+                       cudaStream_t st, ServeLease** out) {
+  RunCfg r = resolve(g);
+  r.mode = BC_MODE_BATCHED;
+  Workspace* w = nullptr;
+  int rc = ws_acquire(g, std::max<uint32_t>(slots, 1), k, st, &w);
+  if (rc) return rc;
+  cudaError_t e = cudaSuccess;
+  if (!w->host_bc) e = cudaMallocHost(&w->host_bc, (size_t)g->n * 8);
+  if (e == cudaSuccess && k) {
+    memcpy(w->host_src, sources, (size_t)k * 4);
+    e = cudaMemcpyAsync(w->src, w->host_src, (size_t)k * 4, cudaMemcpyHostToDevice, st);
+  }
+  if (e != cudaSuccess) {
+    ws_release(g, w, st);
+    return cuda_fail(e, "serve_start");
+  }
+  rc = enqueue_batched(g, w, r, w->src, k, scale, w->bc, nullptr, std::min<uint32_t>(std::max<uint32_t>(slots, 1), w->slots),
+                       0, st, false);
+  if (!rc) {
+    e = cudaMemcpyAsync(w->host_ctl, w->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(w->host_bc, w->bc, (size_t)g->n * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaEventRecord(w->done, st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "serve_start");
+  }
+  if (rc) {
+    ws_release(g, w, st);
+    return rc;
+  }
+  *out = new ServeLease{g, w, st, w->done, k};
+  return BC_OK;
+}
+
+bool bcgpu::serve_ready(ServeLease* l) { return cudaEventQuery(l->ev) != cudaErrorNotReady; }
+
+int bcgpu::serve_finish(ServeLease* l, double* out_bc) {
+  cudaError_t e = cudaEventSynchronize(l->ev);
+  int rc = BC_OK;
+  if (e != cudaSuccess) {
+    rc = cuda_fail(e, "serving run");
+  } else {
+    memcpy(out_bc, l->w->host_bc, (size_t)l->g->n * 8);
+    rc = status_from_dev(l->w->host_ctl->err);
+  }
+  {
+    std::lock_guard<std::mutex> lk(l->g->mu);
+    l->w->busy = false;
+  }
+  delete l;
+  return rc;
+}
 
 // ===================================================================== ABI
 

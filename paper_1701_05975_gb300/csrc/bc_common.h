@@ -102,6 +102,32 @@ cudaError_t launch_fill_slabs(char* base, uint64_t stride, uint32_t nslots, uint
 // Record a message for bc_last_error() on the calling thread; returns code.
 int set_error(int code, const char* msg);
 
+}  // namespace bcgpu
+
+struct bc_graph;
+
+namespace bcgpu {
+
+// Serving support (implemented in bc_api.cu, used by the scheduler in
+// bc_serve.cu).  A lease is one request's run on one stream: its workspace
+// stays reserved until serve_finish copies the result out.
+struct ServeLease;
+struct ServePlan {
+  uint32_t team;        // threads per source
+  uint32_t max_slots;   // sources the GPU holds at once for this team size
+  uint64_t slot_bytes;  // device bytes per source in flight
+  uint64_t fixed_bytes; // per-request device bytes besides the slabs
+};
+int serve_plan(bc_graph* g, ServePlan* out);
+int serve_start(bc_graph* g, const uint32_t* sources, uint32_t k, double scale, uint32_t slots, cudaStream_t st,
+                ServeLease** out);
+bool serve_ready(ServeLease* l);
+int serve_finish(ServeLease* l, double* out_bc);  // releases the lease
+int graph_device(const bc_graph* g);
+uint32_t graph_n(const bc_graph* g);
+uint64_t graph_nnz(const bc_graph* g);
+void graph_serving_ref(bc_graph* g, int delta);
+
 // Plain form (bc_plain.cu): one source at a time over the whole GPU.
 struct PlainWork;
 PlainWork* plain_create(uint32_t n, int dist_bits, cudaError_t* e);
