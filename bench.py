@@ -31,6 +31,9 @@ sys.path.insert(0, ROOT)
 from paper_1701_05975_gb300 import gen  # noqa: E402
 
 WORKLOADS = {
+    "serving": ("serving stream: Poisson arrivals over 15 graphs {ER avg deg 16, BA 4/vertex, perturbed grid} x "
+                "n in {1k, 4k, 16k, 65k, 262k}, weights U[1,1000]; exact BC for n <= 16k, else 256 sampled sources",
+                None),
     "rmat20": ("R-MAT scale 20, edge factor 16, a=.57 b=.19 c=.19, symmetrised, weights U[1,255], "
                "4096 uniform sources, scale 0.5 n/k", gen.workload_rmat20),
     "ba65k": ("Barabasi-Albert n=65536, 4 edges per new vertex, weights U[1,1000], all sources, scale 0.5",
@@ -205,6 +208,103 @@ def run_reference(args, g, sources, scale, desc):
     print(json.dumps(line), flush=True)
 
 
+def run_serving_reference(args, desc):
+    """The oracle over a bounded prefix of the same request stream."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+
+    cores = os.cpu_count() or 1
+    reqs = gen.serving_requests(num=args.requests, rate_per_s=1.0, seed=0)
+    pool = {}
+    done, edges, t_total = 0, 0, 0.0
+    for r in reqs:
+        if t_total > 120.0:
+            break
+        key = (r.kind, r.n)
+        if key not in pool:
+            pool[key] = gen.serving_graph(r.kind, r.n, seed=0)
+        g = pool[key]
+        t0 = time.perf_counter()
+        oracle.bc(g, r.sources, r.scale, nthreads=cores)
+        t_total += time.perf_counter() - t0
+        done += 1
+        edges += len(r.sources) * g.m
+    value = edges / t_total / 1e9
+    line = {"impl": "reference", "metric": "serving: aggregate GTEPS and p50/p99 latency (submit -> done)",
+            "value": value, "unit": "GTEPS", "n_gpus": args.gpus, "steps": 1, "warmup": 0,
+            "ms_per_step": t_total * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "config": {"workload": desc, "requests_timed": done},
+            "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": cores, "kind": "oracle",
+                             "sample": f"first {done} of {len(reqs)} requests, run back to back"},
+            "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_serving(args, desc):
+    """Serving workload: saturated throughput first (a burst of requests),
+    then a Poisson stream at 0.7 of it; p50/p99 from submit to done."""
+    ws, rank, local = dist_env()
+    import torch
+
+    import paper_1701_05975_gb300 as bc
+
+    torch.cuda.set_device(local)
+    pool = {}
+    for kind in gen.SERVING_KINDS:
+        for n in gen.SERVING_SIZES:
+            pool[(kind, n)] = gen.serving_graph(kind, n, seed=0)
+    graphs = {key: bc.Graph(g) for key, g in pool.items()}
+    reqs = gen.serving_requests(num=args.requests, rate_per_s=1.0, seed=0)
+
+    def run_stream(batch, rate):
+        bc.bc_serving_reset()
+        outs, ids = [], []
+        t_start = time.perf_counter()
+        for i, r in enumerate(batch):
+            if rate is not None:
+                due = t_start + r.arrival_s / rate
+                while True:
+                    now = time.perf_counter()
+                    if now >= due:
+                        break
+                    time.sleep(min(due - now, 0.002))
+            out = np.empty(r.n, np.float64)
+            outs.append(out)
+            ids.append(bc.bc_request_submit(graphs[(r.kind, r.n)].handle, r.sources, r.scale, out))
+        for rid in ids:
+            bc.bc_request_wait(rid, -1)
+        makespan = time.perf_counter() - t_start
+        return makespan, bc.bc_serving_stats_get()
+
+    # warm-up: one request per graph (workspace allocation)
+    warm = [gen.ServingRequest(0.0, k, n, np.arange(min(n, 64), dtype=np.uint32), 1.0) for (k, n) in pool]
+    run_stream(warm, None)
+    burst = reqs[: min(200, len(reqs))]
+    mk_sat, _ = run_stream(burst, None)
+    sat_rate = len(burst) / mk_sat
+    rate = 0.7 * sat_rate
+    makespan, st = run_stream(reqs, rate)
+    edges = sum(len(r.sources) * pool[(r.kind, r.n)].m for r in reqs)
+    gteps = edges / makespan / 1e9
+    line = {
+        "metric": "serving: aggregate GTEPS and p50/p99 latency (submit -> done)", "value": gteps, "unit": "GTEPS",
+        "n_gpus": ws, "steps": 1, "warmup": 1, "ms_per_step": makespan * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "requests": len(reqs), "arrival_rate_per_s": rate,
+                   "saturated_rate_per_s": sat_rate, "load": 0.7},
+        "latency_ms": {"p50": st.p50_ms, "p99": st.p99_ms, "mean": st.mean_ms},
+        "completed": int(st.completed), "failed": int(st.failed), "max_concurrent": int(st.max_concurrent),
+        "e2e": {"value": gteps, "unit": "GTEPS", "h2d_bytes_per_step": int(sum(4 * len(r.sources) for r in reqs)),
+                "d2h_bytes_per_step": int(sum(8 * r.n for r in reqs))},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for G in graphs.values():
+        G.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -214,10 +314,18 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-sample", type=int, default=0, help="also time the plain form on this many sources")
-    ap.add_argument("--autotune", type=int, default=0, help="probe sources for the autotuner (0: off)")
+    ap.add_argument("--autotune", type=int, default=-1,
+                    help="probe sources for the autotuner (-1: automatic size, 0: off)")
+    ap.add_argument("--requests", type=int, default=2000, help="serving workload: number of requests")
     args = ap.parse_args()
 
     desc, maker = WORKLOADS[args.workload]
+    if args.workload == "serving":
+        if args.impl == "reference":
+            run_serving_reference(args, desc)
+        else:
+            run_serving(args, desc)
+        return
     g, sources, scale = maker()
     m = g.m
 
@@ -243,8 +351,12 @@ def main():
 
     dev = torch.device("cuda", local)
     G = bc.Graph(g)
-    if args.autotune:
-        G.autotune(sources[: args.autotune])
+    probe = args.autotune if args.autotune >= 0 else min(len(sources), 2048)
+    tune_s = 0.0
+    if probe:
+        t0 = time.perf_counter()
+        G.autotune(sources[:probe])
+        tune_s = time.perf_counter() - t0
     stream = torch.cuda.Stream(device=dev)
     d_src = torch.from_numpy(sources.astype(np.int32)).to(dev)
     d_out = torch.empty(g.n, dtype=torch.float64, device=dev)
@@ -317,7 +429,9 @@ def main():
         "config": {"workload": desc, "n": g.n, "m": m, "nnz": g.nnz, "sources": k, "scale": scale,
                    "l2": "inputs larger than L2 (CSR 251 MB + per-source slabs)",
                    "team_threads": int(st.team_threads), "slots": int(st.slots),
-                   "bucket_width": int(st.bucket_width), "parallelism": f"replicas x{ws}"},
+                   "bucket_width": int(st.bucket_width), "parallelism": f"replicas x{ws}",
+                   "autotune": {"probe_sources": probe, "seconds": round(tune_s, 2)},
+                   "relabeled_by_degree": bool(G.info().relabeled), "dist_bits": int(G.info().dist_bits)},
         "e2e": {"value": ws * k * m / e2e_s / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": 4 * k,
                 "d2h_bytes_per_step": 8 * g.n},
         "gpu_launches": 3 * args.steps,

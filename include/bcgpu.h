@@ -120,6 +120,7 @@ typedef struct bc_graph_info {
   uint32_t dist_bits;     /* 32 or 64: device distance width chosen for this graph */
   uint64_t device_bytes;  /* resident CSR + per-vertex graph data */
   uint64_t slab_bytes;    /* device bytes one in-flight source needs */
+  uint32_t relabeled;     /* 1 when vertices are stored internally in decreasing-degree order */
 } bc_graph_info;
 
 int bc_graph_get_info(bc_graph_t g, bc_graph_info *out);

@@ -51,7 +51,8 @@ class bc_config(ctypes.Structure):
 
 class bc_graph_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint32), ("nnz", ctypes.c_uint64), ("max_weight", ctypes.c_uint32),
-                ("dist_bits", ctypes.c_uint32), ("device_bytes", ctypes.c_uint64), ("slab_bytes", ctypes.c_uint64)]
+                ("dist_bits", ctypes.c_uint32), ("device_bytes", ctypes.c_uint64), ("slab_bytes", ctypes.c_uint64),
+                ("relabeled", ctypes.c_uint32)]
 
 
 class bc_run_stats(ctypes.Structure):

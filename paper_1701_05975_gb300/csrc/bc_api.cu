@@ -121,6 +121,7 @@ struct TuneCfg {
   uint32_t team = 0;
   uint64_t width = 0;
   uint32_t settle_in = 0;
+  uint32_t max_slots = 0;  // 0: the full resident capacity
 };
 
 std::mutex g_tune_mu;
@@ -209,7 +210,7 @@ RunCfg resolve(const bc_graph* g) {
   uint32_t si = c.settle_in ? c.settle_in : (g->tuned.settle_in ? g->tuned.settle_in : 1u);
   r.settle_in = (si == 1u) ? 1u : 0u;
   r.phase_cap = c.phase_cap ? c.phase_cap : 2ull * g->n + 64;
-  r.max_slots = c.max_slots;
+  r.max_slots = c.max_slots ? c.max_slots : g->tuned.max_slots;
   r.mem_fraction = c.mem_fraction > 0 ? c.mem_fraction : 0.6;
   return r;
 }
@@ -729,6 +730,7 @@ int bc_graph_get_info(bc_graph_t g, bc_graph_info* out) {
   out->dist_bits = (uint32_t)g->dist_bits;
   out->device_bytes = g->device_bytes;
   out->slab_bytes = make_layout(g->n, g->dist_bits).stride;
+  out->relabeled = g->relabeled ? 1u : 0u;
   return BC_OK;
 }
 
@@ -883,39 +885,35 @@ int bc_autotune(bc_graph_t g, const uint32_t* sources, uint32_t k_probe) {
   if (!sources || k_probe == 0) return fail(BC_ERR_INVALID, "autotune needs probe sources");
   CK(cudaSetDevice(g->device));
   bc_config user = config_snapshot();
-  const uint32_t teams[] = {32, 128, 256, 512};
+  // candidates: team size x near/far split width, then sources in flight
+  const uint32_t teams[] = {128, 256, 512};
   std::vector<uint64_t> widths;
-  for (uint64_t d : {16ull, 4ull, 1ull}) widths.push_back(std::max<uint64_t>(1, g->max_w / d));
-  widths.push_back(4ull * std::max<uint32_t>(g->max_w, 1));
+  for (uint64_t d : {16ull, 4ull, 1ull}) {
+    const uint64_t wv = std::max<uint64_t>(1, g->max_w / d);
+    if (std::find(widths.begin(), widths.end(), wv) == widths.end()) widths.push_back(wv);
+  }
   std::vector<double> out(g->n);
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
-  float best_ms = 1e30f;
+  auto timed = [&](const RunCfg& r, double* ms) -> int {
+    auto t0 = std::chrono::steady_clock::now();
+    int rc = compute_sync(g, sources, k_probe, 1.0, out.data(), nullptr, r);
+    *ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return rc;
+  };
+  RunCfg base = resolve(g);
+  base.mode = BC_MODE_BATCHED;
+  base.settle_in = 1;
+  double ms = 0;
+  if (int rc = timed(base, &ms)) return rc;  // warm-up: workspace allocation
+  double best_ms = 1e300;
   TuneCfg best;
   for (uint32_t team : teams) {
     if (user.team_threads && user.team_threads != team) continue;
     for (uint64_t width : widths) {
       if (user.bucket_width && user.bucket_width != width) continue;
-      RunCfg r = resolve(g);
+      RunCfg r = base;
       r.team = team;
       r.width = width;
-      r.settle_in = 1;
-      r.mode = BC_MODE_BATCHED;
-      // warm once, then time
-      float ms = 0;
-      for (int rep = 0; rep < 2; ++rep) {
-        cudaEventRecord(e0, g->stream);
-        int rc = compute_sync(g, sources, k_probe, 1.0, out.data(), nullptr, r);
-        cudaEventRecord(e1, g->stream);
-        cudaEventSynchronize(e1);
-        if (rc) {
-          cudaEventDestroy(e0);
-          cudaEventDestroy(e1);
-          return rc;
-        }
-        cudaEventElapsedTime(&ms, e0, e1);
-      }
+      if (int rc = timed(r, &ms)) return rc;
       if (ms < best_ms) {
         best_ms = ms;
         best.team = team;
@@ -924,8 +922,21 @@ int bc_autotune(bc_graph_t g, const uint32_t* sources, uint32_t k_probe) {
       }
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  if (best.team == 0) return fail(BC_ERR_INVALID, "autotune: the configuration pins every candidate out");
+  // sources in flight: the full resident capacity, or half of it
+  if (!user.max_slots) {
+    RunCfg r = base;
+    r.team = best.team;
+    r.width = best.width;
+    uint32_t full = 0;
+    if (int rc = plan_slots(g, r, k_probe, &full)) return rc;
+    r.max_slots = std::max<uint32_t>(1, full / 2);
+    if (int rc = timed(r, &ms)) return rc;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best.max_slots = r.max_slots;
+    }
+  }
   g->tuned = best;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune_cache[g->fingerprint] = best;
