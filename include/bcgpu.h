@@ -226,6 +226,12 @@ typedef struct bc_run_stats {
   uint64_t bucket_width;
   uint64_t dag_edges;       /* shortest-path DAG edges recorded by the forward pass */
   uint64_t pair_overflows;  /* sources whose DAG edge list overflowed (backward fell back to a CSR scan) */
+  uint64_t cycles_expand;   /* SM cycles summed over sources: frontier expansion (sigma pull + relax) */
+  uint64_t cycles_refill;   /* near-queue refills from the far queue */
+  uint64_t cycles_settle;   /* threshold + settle of the near queue */
+  uint64_t cycles_backward; /* dependency accumulation */
+  uint64_t near_scanned;    /* near-queue entries read by threshold and settle */
+  uint64_t far_scanned;     /* far-queue entries read by refills */
 } bc_run_stats;
 
 int bc_last_run_stats(bc_graph_t g, bc_run_stats *out);

@@ -60,7 +60,10 @@ class bc_run_stats(ctypes.Structure):
                 ("reached", ctypes.c_uint64), ("relax_atomics", ctypes.c_uint64),
                 ("entries_scanned", ctypes.c_uint64), ("team_threads", ctypes.c_uint32),
                 ("slots", ctypes.c_uint32), ("bucket_width", ctypes.c_uint64), ("dag_edges", ctypes.c_uint64),
-                ("pair_overflows", ctypes.c_uint64)]
+                ("pair_overflows", ctypes.c_uint64), ("cycles_expand", ctypes.c_uint64),
+                ("cycles_refill", ctypes.c_uint64), ("cycles_settle", ctypes.c_uint64),
+                ("cycles_backward", ctypes.c_uint64), ("near_scanned", ctypes.c_uint64),
+                ("far_scanned", ctypes.c_uint64)]
 
 
 class bc_serving_stats(ctypes.Structure):

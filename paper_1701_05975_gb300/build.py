@@ -41,14 +41,16 @@ def _newer(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=(), out_dir: str | None = None) -> str:
+    build_dir = out_dir or BUILD
+    lib_path = os.path.join(build_dir, "libbcgpu.so")
+    os.makedirs(build_dir, exist_ok=True)
     srcs = sources()
     hdrs = headers()
     objs = []
     jobs = []
     for s in srcs:
-        o = os.path.join(BUILD, os.path.basename(s)[:-3] + ".o")
+        o = os.path.join(build_dir, os.path.basename(s)[:-3] + ".o")
         objs.append(o)
         if force or _newer(o, [s] + hdrs):
             jobs.append([NVCC, *ARCH, *FLAGS, *extra, "-c", s, "-o", o])
@@ -63,9 +65,9 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     if jobs:
         with concurrent.futures.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             list(ex.map(run, jobs))
-    if force or jobs or _newer(LIB, objs):
-        run([NVCC, *ARCH, "-shared", "-o", LIB, *objs, "-lpthread"])
-    return LIB
+    if force or jobs or _newer(lib_path, objs):
+        run([NVCC, *ARCH, "-shared", "-o", lib_path, *objs, "-lpthread"])
+    return lib_path
 
 
 if __name__ == "__main__":

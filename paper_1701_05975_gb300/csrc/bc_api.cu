@@ -356,6 +356,12 @@ void record_stats(bc_graph* g, const Ctl& c, const RunCfg& r, uint32_t slots) {
   g->last.entries_scanned = c.stats[STAT_ENTRIES];
   g->last.dag_edges = c.stats[STAT_DAG_EDGES];
   g->last.pair_overflows = c.stats[STAT_PAIR_OVERFLOW];
+  g->last.cycles_expand = c.stats[STAT_CYC_EXPAND];
+  g->last.cycles_refill = c.stats[STAT_CYC_REFILL];
+  g->last.cycles_settle = c.stats[STAT_CYC_SETTLE];
+  g->last.cycles_backward = c.stats[STAT_CYC_BACKWARD];
+  g->last.near_scanned = c.stats[STAT_NEAR_SCANNED];
+  g->last.far_scanned = c.stats[STAT_FAR_SCANNED];
   g->last.team_threads = r.team;
   g->last.slots = slots;
   g->last.bucket_width = r.width;
@@ -630,15 +636,24 @@ int bc_graph_create(const uint64_t* row_ptr, const uint32_t* col_idx, const uint
     w2.resize(nnz);
     e2o.resize(nnz);
     rp2[0] = 0;
+    std::vector<std::pair<uint32_t, uint32_t>> row;  // (new neighbour id, old entry)
     for (uint32_t i = 0; i < n; ++i) {
       const uint32_t o = n2o[i];
       const uint64_t deg = row_ptr[o + 1] - row_ptr[o];
       rp2[i + 1] = rp2[i] + deg;
+      // each row sorted by new neighbour id: the gathers of one row then walk
+      // the per-source arrays in address order
+      row.resize(deg);
       for (uint64_t j = 0; j < deg; ++j) {
-        const uint64_t eo = row_ptr[o] + j, en = rp2[i] + j;
-        col2[en] = o2n[col_idx[eo]];
-        w2[en] = w[eo];
-        e2o[en] = (uint32_t)eo;
+        const uint64_t eo = row_ptr[o] + j;
+        row[j] = {o2n[col_idx[eo]], (uint32_t)eo};
+      }
+      std::sort(row.begin(), row.end());
+      for (uint64_t j = 0; j < deg; ++j) {
+        const uint64_t en = rp2[i] + j;
+        col2[en] = row[j].first;
+        w2[en] = w[row[j].second];
+        e2o[en] = row[j].second;
       }
     }
     row_ptr = rp2.data();
@@ -797,6 +812,12 @@ int bc_sync_status(bc_graph_t g, void* stream) {
     g->last.entries_scanned = c.stats[STAT_ENTRIES];
     g->last.dag_edges = c.stats[STAT_DAG_EDGES];
     g->last.pair_overflows = c.stats[STAT_PAIR_OVERFLOW];
+    g->last.cycles_expand = c.stats[STAT_CYC_EXPAND];
+    g->last.cycles_refill = c.stats[STAT_CYC_REFILL];
+    g->last.cycles_settle = c.stats[STAT_CYC_SETTLE];
+    g->last.cycles_backward = c.stats[STAT_CYC_BACKWARD];
+    g->last.near_scanned = c.stats[STAT_NEAR_SCANNED];
+    g->last.far_scanned = c.stats[STAT_FAR_SCANNED];
   }
   return status_from_dev(w->host_ctl->err);
 }

@@ -34,7 +34,10 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr uint32_t NONE = 0xffffffffu;
-constexpr int UNROLL = 4;  // independent edge loads in flight per thread
+#ifndef BCGPU_UNROLL
+#define BCGPU_UNROLL 4
+#endif
+constexpr int UNROLL = BCGPU_UNROLL;  // independent edge loads in flight per thread
 
 template <typename D>
 __device__ __forceinline__ D dinf() {
@@ -46,6 +49,21 @@ __device__ __forceinline__ uint64_t ldcg(const uint64_t* p) {
   return (uint64_t)__ldcg(reinterpret_cast<const unsigned long long*>(p));
 }
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
+
+// Gathers of a team's own slab (distances, sigma).  A slab is private to one
+// CTA and every read is ordered after the writes it must see by the team's
+// barrier, so L1-cacheable loads are valid; BCGPU_GATHER_L1=0 keeps them in L2.
+#ifndef BCGPU_GATHER_L1
+#define BCGPU_GATHER_L1 0
+#endif
+template <typename T>
+__device__ __forceinline__ T ldg_slab(const T* p) {
+#if BCGPU_GATHER_L1
+  return *p;
+#else
+  return ldcg(p);
+#endif
+}
 
 __device__ __forceinline__ uint32_t atomic_min_d(uint32_t* p, uint32_t v) { return atomicMin(p, v); }
 __device__ __forceinline__ uint64_t atomic_min_d(uint64_t* p, uint64_t v) {
@@ -263,7 +281,7 @@ __device__ void expand_forward(const BatchArgs& a, const Slab<D>& sl, TeamShared
       }
       D dus[UNROLL];
 #pragma unroll
-      for (int q = 0; q < UNROLL; ++q) dus[q] = (iv[q] != NONE) ? ldcg(&sl.d[ent[q].x]) : INF;
+      for (int q = 0; q < UNROLL; ++q) dus[q] = (iv[q] != NONE) ? ldg_slab(&sl.d[ent[q].x]) : INF;
 #pragma unroll
       for (int q = 0; q < UNROLL; ++q) {
         if (iv[q] == NONE) continue;
@@ -275,7 +293,7 @@ __device__ void expand_forward(const BatchArgs& a, const Slab<D>& sl, TeamShared
         if (du != INF && du + w == dvi) {
           // u is a shortest-path predecessor of v (settled in an earlier
           // batch): pull its sigma and record the DAG edge u -> v
-          atomicAdd(&sh.acc[i], ldcg(&sl.sig[u]));
+          atomicAdd(&sh.acc[i], ldg_slab(&sl.sig[u]));
           const uint32_t pos = atomicAdd(&sh.pair_len, 1u);
           if (pos < sl.pair_cap) sl.pairs[pos] = make_uint2(u, sh.vtx[i]);
           else sh.pair_over = 1;
@@ -402,6 +420,9 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
   const D INF = dinf<D>();
   unsigned long long relax = 0, scanned = 0;
   uint64_t phases = 0, refills = 0;
+  // per-section cycle counters (read by the team leader only)
+  unsigned long long cyc_expand = 0, cyc_refill = 0, cyc_settle = 0, cyc_back = 0, near_sc = 0, far_sc = 0;
+  long long c0 = clock64();
   // Algorithm 1 / 4: d = INF everywhere already (slab invariant)
   if (t == 0) {
     sl.d[s] = 0;
@@ -422,13 +443,17 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
   uint32_t f0 = 0, f1 = 1;
   for (;;) {
     const D split0 = sh.split;
+    c0 = clock64();
     expand_forward<D, TEAM>(a, sl, sh, f0, f1, s, t, split0, relax, scanned);
     // DAG edges into the batch just expanded end here
     if (t == 0) sl.pend[sh.nlev - 1] = sh.pair_len;
+    cyc_expand += clock64() - c0;
+    c0 = clock64();
     // refill the near queue from the far queue when it runs dry
     while (sh.near_len == 0 && sh.far_len > 0) {
       const D old = sh.split;
       const uint32_t fl = sh.far_len;
+      far_sc += 2ull * fl;
       D lo = INF, dummy = INF;
       for (uint32_t base = 0; base < fl; base += TEAM) {
         const uint32_t j = base + t;
@@ -470,9 +495,12 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
       team_sync<TEAM>();
       if (sh.stop) break;
     }
+    cyc_refill += clock64() - c0;
+    c0 = clock64();
     if (sh.stop || sh.near_len == 0) break;
     // threshold: Delta' = min(min_near (D + Delta_node), split) <= Delta_i
     const uint32_t nl = sh.near_len;
+    near_sc += 2ull * nl;
     const D split = sh.split;
     D out = INF, dm = INF;
     for (uint32_t base = 0; base < nl; base += TEAM) {
@@ -517,6 +545,7 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
       if (phases + refills > a.phase_cap) sh.stop = 1;
     }
     team_sync<TEAM>();
+    cyc_settle += clock64() - c0;
     if (sh.stop) break;
     f0 = S0;
     f1 = S0 + nset;
@@ -536,6 +565,7 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
     }
   } else {
     const uint32_t nlev = sh.nlev;
+    c0 = clock64();
     if (!a.ebc && !sh.pair_over) {
       // Algorithm 3 over the recorded DAG edges: levels in reverse; finalize
       // the level's vertices, then push their coefficients to predecessors
@@ -556,6 +586,7 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
         accumulate_level<D, TEAM>(a, sl, sh, b0, b1, s, t, scanned);
       }
     }
+    cyc_back += clock64() - c0;
     // restore the slab invariant: d = INF on every vertex this source reached
     const uint32_t n_reached = sh.S_len;
     for (uint32_t j = t; j < n_reached; j += TEAM) sl.d[ldcg(&sl.S[j])] = INF;
@@ -573,6 +604,12 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
       atomicAdd(&a.stats[STAT_ENTRIES], scanned);
       atomicAdd(&a.stats[STAT_DAG_EDGES], (unsigned long long)sh.pair_len);
       atomicAdd(&a.stats[STAT_PAIR_OVERFLOW], (unsigned long long)sh.pair_over);
+      atomicAdd(&a.stats[STAT_CYC_EXPAND], cyc_expand);
+      atomicAdd(&a.stats[STAT_CYC_REFILL], cyc_refill);
+      atomicAdd(&a.stats[STAT_CYC_SETTLE], cyc_settle);
+      atomicAdd(&a.stats[STAT_CYC_BACKWARD], cyc_back);
+      atomicAdd(&a.stats[STAT_NEAR_SCANNED], near_sc);
+      atomicAdd(&a.stats[STAT_FAR_SCANNED], far_sc);
     }
   }
   team_sync<TEAM>();

@@ -62,6 +62,12 @@ enum : int {
   STAT_ENTRIES,
   STAT_DAG_EDGES,
   STAT_PAIR_OVERFLOW,
+  STAT_CYC_EXPAND,    // SM clock cycles (team leader) spent per section
+  STAT_CYC_REFILL,
+  STAT_CYC_SETTLE,
+  STAT_CYC_BACKWARD,
+  STAT_NEAR_SCANNED,  // near / far queue entries read by the threshold, settle and refill passes
+  STAT_FAR_SCANNED,
   STAT_COUNT
 };
 
