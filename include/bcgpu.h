@@ -85,6 +85,8 @@ typedef struct bc_config {
   uint64_t bucket_width;  /* near/far split width, in distance units (>= 1) */
   uint64_t phase_cap;     /* device cap on phases per source; hitting it returns BC_ERR_TIMEOUT */
   double mem_fraction;    /* share of free device memory the slabs may take (0 < f <= 0.95) */
+  uint32_t warp_degree;   /* forward expansion: rows with at least this many entries get one warp each */
+  uint32_t team_degree;   /* ... and rows with at least this many entries the whole team (>= warp_degree) */
 } bc_config;
 
 /* Read the current process-wide configuration. */

@@ -46,7 +46,7 @@ class BCError(RuntimeError):
 class bc_config(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_uint32), ("team_threads", ctypes.c_uint32), ("max_slots", ctypes.c_uint32),
                 ("settle_in", ctypes.c_uint32), ("bucket_width", ctypes.c_uint64), ("phase_cap", ctypes.c_uint64),
-                ("mem_fraction", ctypes.c_double)]
+                ("mem_fraction", ctypes.c_double), ("warp_degree", ctypes.c_uint32), ("team_degree", ctypes.c_uint32)]
 
 
 class bc_graph_info(ctypes.Structure):

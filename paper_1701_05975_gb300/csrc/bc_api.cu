@@ -54,7 +54,7 @@ int cuda_fail(cudaError_t e, const char* where) {
   } while (0)
 
 std::mutex g_cfg_mu;
-bc_config g_cfg = {BC_MODE_BATCHED, 0, 0, 0, 0, 0, 0.0};
+bc_config g_cfg = {BC_MODE_BATCHED, 0, 0, 0, 0, 0, 0.0, 0, 0};
 
 bc_config config_snapshot() {
   std::lock_guard<std::mutex> lk(g_cfg_mu);
@@ -122,6 +122,8 @@ struct TuneCfg {
   uint64_t width = 0;
   uint32_t settle_in = 0;
   uint32_t max_slots = 0;  // 0: the full resident capacity
+  uint32_t warp_deg = 0;
+  uint32_t team_deg = 0;
 };
 
 std::mutex g_tune_mu;
@@ -194,6 +196,8 @@ struct RunCfg {
   uint32_t max_slots;
   double mem_fraction;
   uint32_t mode;
+  uint32_t warp_deg;
+  uint32_t team_deg;
 };
 
 RunCfg resolve(const bc_graph* g) {
@@ -212,6 +216,9 @@ RunCfg resolve(const bc_graph* g) {
   r.phase_cap = c.phase_cap ? c.phase_cap : 2ull * g->n + 64;
   r.max_slots = c.max_slots ? c.max_slots : g->tuned.max_slots;
   r.mem_fraction = c.mem_fraction > 0 ? c.mem_fraction : 0.6;
+  r.warp_deg = c.warp_degree ? c.warp_degree : (g->tuned.warp_deg ? g->tuned.warp_deg : 32u);
+  r.team_deg = c.team_degree ? c.team_degree : (g->tuned.team_deg ? g->tuned.team_deg : 8u * r.team);
+  r.team_deg = std::max(r.team_deg, r.warp_deg);
   return r;
 }
 
@@ -317,6 +324,8 @@ BatchArgs make_args(bc_graph* g, Workspace* w, const RunCfg& r, const uint32_t* 
   a.stats = w->ctl->stats;
   a.flags = flags;
   a.debug_out = w->ctl->debug;
+  a.warp_deg = r.warp_deg;
+  a.team_deg = r.team_deg;
   return a;
 }
 
@@ -570,6 +579,8 @@ int bc_set_config(const bc_config* cfg) {
     return fail(BC_ERR_INVALID, "team_threads must be 0, 32, 128, 256 or 512");
   if (cfg->settle_in > 2) return fail(BC_ERR_INVALID, "settle_in must be 0, 1 or 2");
   if (cfg->mem_fraction < 0 || cfg->mem_fraction > 0.95) return fail(BC_ERR_INVALID, "mem_fraction out of range");
+  if (cfg->team_degree && cfg->warp_degree && cfg->team_degree < cfg->warp_degree)
+    return fail(BC_ERR_INVALID, "team_degree must be >= warp_degree");
   std::lock_guard<std::mutex> lk(g_cfg_mu);
   g_cfg = *cfg;
   return BC_OK;

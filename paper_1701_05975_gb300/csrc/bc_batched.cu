@@ -101,8 +101,12 @@ struct TeamShared {
   D dv[TEAM];
   double acc[TEAM];
   double sv[TEAM];
+  uint32_t dg[TEAM];     // degree of each chunk vertex
+  uint32_t wlist[TEAM];  // chunk vertices walked by one warp each
+  uint32_t tlist[TEAM];  // chunk vertices walked by the whole team
+  uint32_t wnext, nwl, ntl;
   D red[2 * (TEAM / 32) + 2];
-  uint32_t scan[TEAM / 32 + 1];
+  uint32_t scan[2 * (TEAM / 32 + 1)];
 };
 
 template <int TEAM>
@@ -148,6 +152,45 @@ __device__ __forceinline__ uint32_t team_excl_scan(uint32_t x, uint32_t* total, 
     uint32_t r = scratch[w] + inc - x;
     __syncthreads();
     return r;
+  }
+}
+
+// Two exclusive prefix sums at once (shares the barriers).
+template <int TEAM>
+__device__ __forceinline__ void team_excl_scan2(uint32_t x, uint32_t y, uint32_t* ex, uint32_t* ey, uint32_t* tx,
+                                                uint32_t* ty, uint32_t* scratch) {
+  const uint32_t ix = warp_incl_scan(x), iy = warp_incl_scan(y);
+  if constexpr (TEAM == 32) {
+    *tx = __shfl_sync(FULL, ix, 31);
+    *ty = __shfl_sync(FULL, iy, 31);
+    *ex = ix - x;
+    *ey = iy - y;
+  } else {
+    constexpr int NW = TEAM / 32;
+    const int w = (threadIdx.x % TEAM) >> 5, lane = threadIdx.x & 31;
+    if (lane == 31) {
+      scratch[w] = ix;
+      scratch[NW + 1 + w] = iy;
+    }
+    __syncthreads();
+    if (w == 0) {
+      const uint32_t vx = lane < NW ? scratch[lane] : 0u, vy = lane < NW ? scratch[NW + 1 + lane] : 0u;
+      const uint32_t sx = warp_incl_scan(vx), sy = warp_incl_scan(vy);
+      if (lane < NW) {
+        scratch[lane] = sx - vx;
+        scratch[NW + 1 + lane] = sy - vy;
+      }
+      if (lane == NW - 1) {
+        scratch[NW] = sx;
+        scratch[2 * NW + 1] = sy;
+      }
+    }
+    __syncthreads();
+    *tx = scratch[NW];
+    *ty = scratch[2 * NW + 1];
+    *ex = scratch[w] + ix - x;
+    *ey = scratch[NW + 1 + w] + iy - y;
+    __syncthreads();
   }
 }
 
@@ -254,19 +297,131 @@ __device__ __forceinline__ uint32_t owner_of(const uint32_t* off, uint32_t cnt, 
   return lo;
 }
 
-// Forward expansion of the batch S[f0, f1): sigma pull + relaxation.
+// One CSR entry {u, w} of chunk vertex i during the forward pass: if u is a
+// shortest-path predecessor (settled in an earlier batch), pull its sigma and
+// record the DAG edge u -> v; otherwise relax u.
+template <typename D, int TEAM>
+__device__ __forceinline__ void visit_entry(const Slab<D>& sl, TeamShared<D, TEAM>& sh, uint32_t i, uint2 ent, D du,
+                                            D split, unsigned long long& relax) {
+  const D INF = dinf<D>();
+  const uint32_t u = ent.x;
+  const D w = (D)ent.y;
+  const D dvi = sh.dv[i];
+  if (du != INF && du + w == dvi) {
+    atomicAdd(&sh.acc[i], ldg_slab(&sl.sig[u]));
+    const uint32_t pos = atomicAdd(&sh.pair_len, 1u);
+    if (pos < sl.pair_cap) sl.pairs[pos] = make_uint2(u, sh.vtx[i]);
+    else sh.pair_over = 1;
+  } else {
+    const D nd = dvi + w;
+    if (nd < du) {
+      ++relax;
+      const D old = atomic_min_d(&sl.d[u], nd);
+      if (nd < old) {
+        if (old == INF) {
+          if (nd < split) {
+            sl.nearq[atomicAdd(&sh.near_len, 1u)] = u;
+          } else {
+            sl.farq[atomicAdd(&sh.far_len, 1u)] = u;
+          }
+        } else if (old >= split && nd < split) {
+          sl.nearq[atomicAdd(&sh.near_len, 1u)] = u;
+        }
+      }
+    }
+  }
+}
+
+// `lanes` threads (this one is number l) walk the whole row of chunk vertex i,
+// UNROLL independent adjacency loads and distance gathers in flight each.
+template <typename D, int TEAM>
+__device__ __forceinline__ void walk_row(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, TEAM>& sh, uint32_t i,
+                                         uint32_t l, uint32_t lanes, D split, unsigned long long& relax) {
+  const D INF = dinf<D>();
+  const uint64_t r0 = sh.rs[i];
+  const uint32_t deg = sh.dg[i];
+  for (uint32_t e0 = l; e0 < deg; e0 += lanes * UNROLL) {
+    uint2 ent[UNROLL];
+#pragma unroll
+    for (int q = 0; q < UNROLL; ++q) {
+      const uint32_t e = e0 + q * lanes;
+      ent[q] = e < deg ? __ldg(&a.g.adj[r0 + e]) : make_uint2(0, 0);
+    }
+    D dus[UNROLL];
+#pragma unroll
+    for (int q = 0; q < UNROLL; ++q) dus[q] = (e0 + q * lanes < deg) ? ldg_slab(&sl.d[ent[q].x]) : INF;
+#pragma unroll
+    for (int q = 0; q < UNROLL; ++q)
+      if (e0 + q * lanes < deg) visit_entry<D, TEAM>(sl, sh, i, ent[q], dus[q], split, relax);
+  }
+}
+
+// Forward expansion of the batch S[f0, f1): sigma pull + relaxation.  Each
+// chunk of up to TEAM vertices is split by degree: rows of at least
+// team_deg entries are walked by the whole team one after another, rows of
+// at least warp_deg entries by one warp each (taken dynamically), and the
+// remaining short rows are spread edge by edge over all threads (a degree
+// scan plus a binary search for each edge's row).  No barrier separates the
+// tiers, so threads that finish one move on to the next.
 template <typename D, int TEAM>
 __device__ void expand_forward(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, TEAM>& sh, uint32_t f0,
                                uint32_t f1, uint32_t s, int t, D split, unsigned long long& relax,
                                unsigned long long& scanned) {
   const D INF = dinf<D>();
+  const uint32_t warp_deg = a.warp_deg;
+  const uint32_t team_deg = (TEAM == 32) ? a.warp_deg : a.team_deg;
   for (uint32_t base = f0; base < f1; base += TEAM) {
     const uint32_t cnt = min((uint32_t)TEAM, f1 - base);
-    const uint32_t total = load_chunk<D, TEAM>(a, sl, sh, base, cnt, t, false);
-    scanned += (t == 0) ? total : 0;
-    // ILP: each thread first issues UNROLL independent adjacency loads, then
-    // UNROLL independent distance gathers, then processes them
-    for (uint32_t e0 = t; e0 < total; e0 += TEAM * UNROLL) {
+    uint32_t deg = 0, small = 0, is_w = 0, is_t = 0;
+    if ((uint32_t)t < cnt) {
+      const uint32_t v = ldcg(&sl.S[base + t]);
+      const uint64_t r0 = __ldg(&a.g.row_ptr[v]);
+      deg = (uint32_t)(__ldg(&a.g.row_ptr[v + 1]) - r0);
+      sh.vtx[t] = v;
+      sh.rs[t] = r0;
+      sh.dg[t] = deg;
+      sh.dv[t] = ldcg(&sl.d[v]);
+      sh.acc[t] = 0.0;
+      if (deg >= team_deg) is_t = 1;
+      else if (deg >= warp_deg) is_w = 1;
+      else small = deg;
+    }
+    uint32_t ex_small, ex_tier, total_small, tiers;
+    // the tier counts are packed: warp-walked in the low 16 bits, team-walked above
+    team_excl_scan2<TEAM>(small, is_w | (is_t << 16), &ex_small, &ex_tier, &total_small, &tiers, sh.scan);
+    if ((uint32_t)t < cnt) {
+      sh.off[t] = ex_small;
+      if (is_w) sh.wlist[ex_tier & 0xffffu] = t;
+      if (is_t) sh.tlist[ex_tier >> 16] = t;
+    }
+    if (t == 0) {
+      sh.off[cnt] = total_small;
+      sh.wnext = 0;
+    }
+    team_sync<TEAM>();
+    const uint32_t nw = tiers & 0xffffu, nt = tiers >> 16;
+    scanned += (t == 0) ? (uint64_t)total_small : 0;
+    // tier 3: whole team per row
+    for (uint32_t h = 0; h < nt; ++h) {
+      const uint32_t i = sh.tlist[h];
+      if (t == 0) scanned += sh.dg[i];
+      walk_row<D, TEAM>(a, sl, sh, i, (uint32_t)t, TEAM, split, relax);
+    }
+    // tier 2: one warp per row, rows taken in turn
+    if constexpr (TEAM > 32) {
+      const uint32_t lane = threadIdx.x & 31;
+      for (;;) {
+        uint32_t wi = 0;
+        if (lane == 0) wi = atomicAdd(&sh.wnext, 1u);
+        wi = __shfl_sync(FULL, wi, 0);
+        if (wi >= nw) break;
+        const uint32_t i = sh.wlist[wi];
+        if (lane == 0) scanned += sh.dg[i];
+        walk_row<D, TEAM>(a, sl, sh, i, lane, 32, split, relax);
+      }
+    }
+    // tier 1: short rows, edge-parallel over the whole team
+    for (uint32_t e0 = t; e0 < total_small; e0 += TEAM * UNROLL) {
       uint32_t iv[UNROLL];
       uint2 ent[UNROLL];
 #pragma unroll
@@ -274,7 +429,7 @@ __device__ void expand_forward(const BatchArgs& a, const Slab<D>& sl, TeamShared
         const uint32_t e = e0 + q * TEAM;
         iv[q] = NONE;
         ent[q] = make_uint2(0, 0);
-        if (e < total) {
+        if (e < total_small) {
           iv[q] = owner_of<TEAM>(sh.off, cnt, e);
           ent[q] = __ldg(&a.g.adj[sh.rs[iv[q]] + (e - sh.off[iv[q]])]);
         }
@@ -283,39 +438,8 @@ __device__ void expand_forward(const BatchArgs& a, const Slab<D>& sl, TeamShared
 #pragma unroll
       for (int q = 0; q < UNROLL; ++q) dus[q] = (iv[q] != NONE) ? ldg_slab(&sl.d[ent[q].x]) : INF;
 #pragma unroll
-      for (int q = 0; q < UNROLL; ++q) {
-        if (iv[q] == NONE) continue;
-        const uint32_t i = iv[q];
-        const uint32_t u = ent[q].x;
-        const D w = (D)ent[q].y;
-        const D dvi = sh.dv[i];
-        const D du = dus[q];
-        if (du != INF && du + w == dvi) {
-          // u is a shortest-path predecessor of v (settled in an earlier
-          // batch): pull its sigma and record the DAG edge u -> v
-          atomicAdd(&sh.acc[i], ldg_slab(&sl.sig[u]));
-          const uint32_t pos = atomicAdd(&sh.pair_len, 1u);
-          if (pos < sl.pair_cap) sl.pairs[pos] = make_uint2(u, sh.vtx[i]);
-          else sh.pair_over = 1;
-        } else {
-          const D nd = dvi + w;
-          if (nd < du) {
-            ++relax;
-            const D old = atomic_min_d(&sl.d[u], nd);
-            if (nd < old) {
-              if (old == INF) {
-                if (nd < split) {
-                  sl.nearq[atomicAdd(&sh.near_len, 1u)] = u;
-                } else {
-                  sl.farq[atomicAdd(&sh.far_len, 1u)] = u;
-                }
-              } else if (old >= split && nd < split) {
-                sl.nearq[atomicAdd(&sh.near_len, 1u)] = u;
-              }
-            }
-          }
-        }
-      }
+      for (int q = 0; q < UNROLL; ++q)
+        if (iv[q] != NONE) visit_entry<D, TEAM>(sl, sh, iv[q], ent[q], dus[q], split, relax);
     }
     team_sync<TEAM>();
     if ((uint32_t)t < cnt && sh.vtx[t] != s) sl.sig[sh.vtx[t]] = sh.acc[t];
@@ -592,16 +716,21 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
     for (uint32_t j = t; j < n_reached; j += TEAM) sl.d[ldcg(&sl.S[j])] = INF;
   }
   if (a.stats) {
-    // relax is per thread; the rest are uniform (counted once)
+    // relax and scanned are per thread; the rest are uniform (counted once)
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) relax += __shfl_xor_sync(FULL, relax, o);
-    if ((t & 31) == 0) atomicAdd(&a.stats[STAT_RELAX], relax);
+    for (int o = 16; o > 0; o >>= 1) {
+      relax += __shfl_xor_sync(FULL, relax, o);
+      scanned += __shfl_xor_sync(FULL, scanned, o);
+    }
+    if ((t & 31) == 0) {
+      atomicAdd(&a.stats[STAT_RELAX], relax);
+      atomicAdd(&a.stats[STAT_ENTRIES], scanned);
+    }
     if (t == 0) {
       atomicAdd(&a.stats[STAT_SOURCES], 1ull);
       atomicAdd(&a.stats[STAT_PHASES], (unsigned long long)phases);
       atomicAdd(&a.stats[STAT_REFILLS], (unsigned long long)refills);
       atomicAdd(&a.stats[STAT_REACHED], (unsigned long long)sh.S_len);
-      atomicAdd(&a.stats[STAT_ENTRIES], scanned);
       atomicAdd(&a.stats[STAT_DAG_EDGES], (unsigned long long)sh.pair_len);
       atomicAdd(&a.stats[STAT_PAIR_OVERFLOW], (unsigned long long)sh.pair_over);
       atomicAdd(&a.stats[STAT_CYC_EXPAND], cyc_expand);

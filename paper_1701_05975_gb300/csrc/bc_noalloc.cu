@@ -212,6 +212,8 @@ extern "C" int bc_compute_noalloc(const uint64_t* d_row_ptr, const uint32_t* d_c
     a.stats = ctl->stats;
     a.flags = 0;
     a.debug_out = ctl->debug;
+    a.warp_deg = cfg.warp_degree ? cfg.warp_degree : 32u;
+    a.team_deg = std::max<uint32_t>(cfg.team_degree ? cfg.team_degree : 8u * team, a.warp_deg);
     const int grid = (int)((slots + per_block - 1) / per_block);
     e = launch_batched(a, 64, team, grid, st);
   }
