@@ -140,6 +140,8 @@ struct bc_graph {
   int sm_count = 0;
   uint64_t* row_ptr = nullptr;
   uint2* adj = nullptr;
+  uint32_t* adjp = nullptr;  // packed 32-bit entries when neighbour and weight fit
+  uint32_t col_bits = 0;
   uint32_t* dnode = nullptr;
   double* ebc = nullptr;  // lazily allocated [nnz]
   bool relabeled = false;
@@ -167,6 +169,8 @@ GraphDev view(const bc_graph* g) {
   v.nnz = g->nnz;
   v.row_ptr = g->row_ptr;
   v.adj = g->adj;
+  v.adjp = g->adjp;
+  v.col_bits = g->col_bits;
   v.dnode = g->dnode;
   v.o2n = g->o2n;
   v.n2o = g->n2o;
@@ -688,7 +692,17 @@ int bc_graph_create(const uint64_t* row_ptr, const uint32_t* col_idx, const uint
   uint32_t* d_w = nullptr;
   cudaError_t e = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMalloc(&g->row_ptr, ((size_t)n + 1) * 8);
-  if (e == cudaSuccess) e = cudaMalloc(&g->adj, std::max<size_t>(nnz, 1) * 8);
+  // packed adjacency when bits(n - 1) + bits(max weight) <= 32
+  uint32_t col_bits = 1, w_bits = 1;
+  while (col_bits < 32 && (1ull << col_bits) < (uint64_t)n) ++col_bits;
+  while (w_bits < 32 && (1ull << w_bits) <= (uint64_t)max_w) ++w_bits;
+  const bool packed = col_bits + w_bits <= 32 && g->dist_bits == 32;
+  if (packed) {
+    g->col_bits = col_bits;
+    if (e == cudaSuccess) e = cudaMalloc(&g->adjp, std::max<size_t>(nnz, 1) * 4);
+  } else {
+    if (e == cudaSuccess) e = cudaMalloc(&g->adj, std::max<size_t>(nnz, 1) * 8);
+  }
   if (e == cudaSuccess) e = cudaMalloc(&g->dnode, (size_t)n * 4);
   if (e == cudaSuccess) e = cudaMalloc(&d_col, std::max<size_t>(nnz, 1) * 4);
   if (e == cudaSuccess) e = cudaMalloc(&d_w, std::max<size_t>(nnz, 1) * 4);
@@ -706,12 +720,14 @@ int bc_graph_create(const uint64_t* row_ptr, const uint32_t* col_idx, const uint
     g->h_o2n = o2n;
   }
   if (e == cudaSuccess) e = launch_prep(n, nnz, g->row_ptr, d_col, d_w, g->adj, g->dnode, g->stream);
+  if (e == cudaSuccess && packed) e = launch_pack32(nnz, d_col, d_w, col_bits, g->adjp, g->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
   cudaFree(d_col);
   cudaFree(d_w);
   if (e != cudaSuccess) {
     cudaFree(g->row_ptr);
     cudaFree(g->adj);
+    cudaFree(g->adjp);
     cudaFree(g->dnode);
     cudaFree(g->o2n);
     cudaFree(g->n2o);
@@ -719,7 +735,8 @@ int bc_graph_create(const uint64_t* row_ptr, const uint32_t* col_idx, const uint
     if (g->stream) cudaStreamDestroy(g->stream);
     return cuda_fail(e, "bc_graph_create upload");
   }
-  g->device_bytes = ((uint64_t)n + 1) * 8 + nnz * 8 + (uint64_t)n * 4 + (relabel ? 8ull * n + 4ull * nnz : 0);
+  g->device_bytes = ((uint64_t)n + 1) * 8 + nnz * (packed ? 4 : 8) + (uint64_t)n * 4 +
+                    (relabel ? 8ull * n + 4ull * nnz : 0);
   *out = g.release();
   return BC_OK;
 }
@@ -737,6 +754,7 @@ int bc_graph_destroy(bc_graph_t g) {
   plain_destroy(g->plain);
   cudaFree(g->row_ptr);
   cudaFree(g->adj);
+  cudaFree(g->adjp);
   cudaFree(g->dnode);
   cudaFree(g->ebc);
   cudaFree(g->o2n);

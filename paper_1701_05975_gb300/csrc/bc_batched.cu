@@ -230,6 +230,18 @@ __device__ __forceinline__ void team_min2(D& a, D& b, D* scratch) {
   }
 }
 
+// CSR entry e as {neighbour, weight}: from the packed 32-bit form
+// (neighbour | weight << col_bits) when PACKED, else from {col, w} records.
+template <bool PACKED>
+__device__ __forceinline__ uint2 load_entry(const GraphDev& g, uint64_t e) {
+  if constexpr (PACKED) {
+    const uint32_t x = __ldg(&g.adjp[e]);
+    return make_uint2(x & ((1u << g.col_bits) - 1u), x >> g.col_bits);
+  } else {
+    return __ldg(&g.adj[e]);
+  }
+}
+
 template <typename D>
 struct Slab {
   D* d;
@@ -334,7 +346,7 @@ __device__ __forceinline__ void visit_entry(const Slab<D>& sl, TeamShared<D, TEA
 
 // `lanes` threads (this one is number l) walk the whole row of chunk vertex i,
 // UNROLL independent adjacency loads and distance gathers in flight each.
-template <typename D, int TEAM>
+template <typename D, int TEAM, bool PACKED>
 __device__ __forceinline__ void walk_row(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, TEAM>& sh, uint32_t i,
                                          uint32_t l, uint32_t lanes, D split, unsigned long long& relax) {
   const D INF = dinf<D>();
@@ -345,7 +357,7 @@ __device__ __forceinline__ void walk_row(const BatchArgs& a, const Slab<D>& sl, 
 #pragma unroll
     for (int q = 0; q < UNROLL; ++q) {
       const uint32_t e = e0 + q * lanes;
-      ent[q] = e < deg ? __ldg(&a.g.adj[r0 + e]) : make_uint2(0, 0);
+      ent[q] = e < deg ? load_entry<PACKED>(a.g, r0 + e) : make_uint2(0, 0);
     }
     D dus[UNROLL];
 #pragma unroll
@@ -363,7 +375,7 @@ __device__ __forceinline__ void walk_row(const BatchArgs& a, const Slab<D>& sl, 
 // remaining short rows are spread edge by edge over all threads (a degree
 // scan plus a binary search for each edge's row).  No barrier separates the
 // tiers, so threads that finish one move on to the next.
-template <typename D, int TEAM>
+template <typename D, int TEAM, bool PACKED>
 __device__ void expand_forward(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, TEAM>& sh, uint32_t f0,
                                uint32_t f1, uint32_t s, int t, D split, unsigned long long& relax,
                                unsigned long long& scanned) {
@@ -405,7 +417,7 @@ __device__ void expand_forward(const BatchArgs& a, const Slab<D>& sl, TeamShared
     for (uint32_t h = 0; h < nt; ++h) {
       const uint32_t i = sh.tlist[h];
       if (t == 0) scanned += sh.dg[i];
-      walk_row<D, TEAM>(a, sl, sh, i, (uint32_t)t, TEAM, split, relax);
+      walk_row<D, TEAM, PACKED>(a, sl, sh, i, (uint32_t)t, TEAM, split, relax);
     }
     // tier 2: one warp per row, rows taken in turn
     if constexpr (TEAM > 32) {
@@ -417,7 +429,7 @@ __device__ void expand_forward(const BatchArgs& a, const Slab<D>& sl, TeamShared
         if (wi >= nw) break;
         const uint32_t i = sh.wlist[wi];
         if (lane == 0) scanned += sh.dg[i];
-        walk_row<D, TEAM>(a, sl, sh, i, lane, 32, split, relax);
+        walk_row<D, TEAM, PACKED>(a, sl, sh, i, lane, 32, split, relax);
       }
     }
     // tier 1: short rows, edge-parallel over the whole team
@@ -431,7 +443,7 @@ __device__ void expand_forward(const BatchArgs& a, const Slab<D>& sl, TeamShared
         ent[q] = make_uint2(0, 0);
         if (e < total_small) {
           iv[q] = owner_of<TEAM>(sh.off, cnt, e);
-          ent[q] = __ldg(&a.g.adj[sh.rs[iv[q]] + (e - sh.off[iv[q]])]);
+          ent[q] = load_entry<PACKED>(a.g, sh.rs[iv[q]] + (e - sh.off[iv[q]]));
         }
       }
       D dus[UNROLL];
@@ -448,7 +460,7 @@ __device__ void expand_forward(const BatchArgs& a, const Slab<D>& sl, TeamShared
 }
 
 // Backward (Algorithm 3) over one level S[f0, f1).
-template <typename D, int TEAM>
+template <typename D, int TEAM, bool PACKED>
 __device__ void accumulate_level(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, TEAM>& sh, uint32_t f0,
                                  uint32_t f1, uint32_t s, int t, unsigned long long& scanned) {
   const D INF = dinf<D>();
@@ -470,7 +482,7 @@ __device__ void accumulate_level(const BatchArgs& a, const Slab<D>& sl, TeamShar
         if (e < total) {
           iv[q] = owner_of<TEAM>(sh.off, cnt, e);
           entry[q] = sh.rs[iv[q]] + (e - sh.off[iv[q]]);
-          ent[q] = __ldg(&a.g.adj[entry[q]]);
+          ent[q] = load_entry<PACKED>(a.g, entry[q]);
         }
       }
       D dus[UNROLL];
@@ -539,7 +551,7 @@ __device__ __forceinline__ void push_level_pairs(const uint2* pairs, double* bac
 }
 
 // Returns false when the source hit the phase cap (its slab is then dirty).
-template <typename D, int TEAM>
+template <typename D, int TEAM, bool PACKED>
 __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, TEAM>& sh, uint32_t s, int t) {
   const D INF = dinf<D>();
   unsigned long long relax = 0, scanned = 0;
@@ -568,7 +580,7 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
   for (;;) {
     const D split0 = sh.split;
     c0 = clock64();
-    expand_forward<D, TEAM>(a, sl, sh, f0, f1, s, t, split0, relax, scanned);
+    expand_forward<D, TEAM, PACKED>(a, sl, sh, f0, f1, s, t, split0, relax, scanned);
     // DAG edges into the batch just expanded end here
     if (t == 0) sl.pend[sh.nlev - 1] = sh.pair_len;
     cyc_expand += clock64() - c0;
@@ -707,7 +719,7 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
       for (int lev = (int)nlev - 1; lev >= last; --lev) {
         const uint32_t b0 = ldcg(&sl.ends[lev]);
         const uint32_t b1 = ldcg(&sl.ends[lev + 1]);
-        accumulate_level<D, TEAM>(a, sl, sh, b0, b1, s, t, scanned);
+        accumulate_level<D, TEAM, PACKED>(a, sl, sh, b0, b1, s, t, scanned);
       }
     }
     cyc_back += clock64() - c0;
@@ -746,7 +758,7 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
 }
 
 
-template <typename D, int TEAM, int BLOCK>
+template <typename D, int TEAM, int BLOCK, bool PACKED>
 __global__ void __launch_bounds__(BLOCK) bc_batched_kernel(const BatchArgs a) {
   static_assert(TEAM == 32 || TEAM == BLOCK, "a CTA holds either warp teams or one team");
   constexpr int NTEAMS = BLOCK / TEAM;
@@ -769,35 +781,35 @@ __global__ void __launch_bounds__(BLOCK) bc_batched_kernel(const BatchArgs a) {
       continue;
     }
     if (a.g.o2n) s = __ldg(&a.g.o2n[s]);
-    const bool ok = run_source<D, TEAM>(a, sl, sh, s, t);
+    const bool ok = run_source<D, TEAM, PACKED>(a, sl, sh, s, t);
     if (!ok || (a.flags & RUN_FORWARD_ONLY)) break;
   }
 }
 
-template <typename D, int TEAM, int BLOCK>
+template <typename D, int TEAM, int BLOCK, bool PACKED>
 cudaError_t launch_t(const BatchArgs& a, int grid, cudaStream_t st) {
-  bc_batched_kernel<D, TEAM, BLOCK><<<grid, BLOCK, 0, st>>>(a);
+  bc_batched_kernel<D, TEAM, BLOCK, PACKED><<<grid, BLOCK, 0, st>>>(a);
   return cudaGetLastError();
 }
 
-template <typename D>
+template <typename D, bool PACKED>
 cudaError_t launch_d(const BatchArgs& a, int team, int grid, cudaStream_t st) {
   switch (team) {
-    case 32: return launch_t<D, 32, 256>(a, grid, st);
-    case 128: return launch_t<D, 128, 128>(a, grid, st);
-    case 256: return launch_t<D, 256, 256>(a, grid, st);
-    case 512: return launch_t<D, 512, 512>(a, grid, st);
+    case 32: return launch_t<D, 32, 256, PACKED>(a, grid, st);
+    case 128: return launch_t<D, 128, 128, PACKED>(a, grid, st);
+    case 256: return launch_t<D, 256, 256, PACKED>(a, grid, st);
+    case 512: return launch_t<D, 512, 512, PACKED>(a, grid, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
-template <typename D>
+template <typename D, bool PACKED>
 cudaError_t occ_d(int team, int* out) {
   switch (team) {
-    case 32: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, bc_batched_kernel<D, 32, 256>, 256, 0);
-    case 128: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, bc_batched_kernel<D, 128, 128>, 128, 0);
-    case 256: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, bc_batched_kernel<D, 256, 256>, 256, 0);
-    case 512: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, bc_batched_kernel<D, 512, 512>, 512, 0);
+    case 32: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, bc_batched_kernel<D, 32, 256, PACKED>, 256, 0);
+    case 128: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, bc_batched_kernel<D, 128, 128, PACKED>, 128, 0);
+    case 256: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, bc_batched_kernel<D, 256, 256, PACKED>, 256, 0);
+    case 512: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, bc_batched_kernel<D, 512, 512, PACKED>, 512, 0);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -806,13 +818,23 @@ cudaError_t occ_d(int team, int* out) {
 
 int batched_block_threads(int team) { return team == 32 ? 256 : team; }
 
+// Packed adjacency is only generated for graphs with 32-bit distances.
 cudaError_t launch_batched(const BatchArgs& a, int dist_bits, int team, int grid, cudaStream_t st) {
   if (grid <= 0) return cudaSuccess;
-  return dist_bits == 32 ? launch_d<uint32_t>(a, team, grid, st) : launch_d<uint64_t>(a, team, grid, st);
+  if (dist_bits == 32)
+    return a.g.adjp ? launch_d<uint32_t, true>(a, team, grid, st) : launch_d<uint32_t, false>(a, team, grid, st);
+  if (a.g.adjp) return cudaErrorInvalidValue;
+  return launch_d<uint64_t, false>(a, team, grid, st);
 }
 
+// Resident CTAs per SM; for 32-bit distances the smaller of the two adjacency forms.
 cudaError_t batched_occupancy(int dist_bits, int team, int* blocks_per_sm) {
-  return dist_bits == 32 ? occ_d<uint32_t>(team, blocks_per_sm) : occ_d<uint64_t>(team, blocks_per_sm);
+  if (dist_bits != 32) return occ_d<uint64_t, false>(team, blocks_per_sm);
+  int a = 0, b = 0;
+  cudaError_t e = occ_d<uint32_t, false>(team, &a);
+  if (e == cudaSuccess) e = occ_d<uint32_t, true>(team, &b);
+  *blocks_per_sm = a < b ? a : b;
+  return e;
 }
 
 }  // namespace bcgpu

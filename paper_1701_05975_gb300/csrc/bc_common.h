@@ -14,7 +14,9 @@ struct GraphDev {
   uint32_t n;
   uint64_t nnz;
   const uint64_t* row_ptr;  // [n + 1]
-  const uint2* adj;         // [nnz] {neighbour, weight}
+  const uint2* adj;         // [nnz] {neighbour, weight}, or nullptr when adjp is used
+  const uint32_t* adjp;     // [nnz] neighbour | weight << col_bits (graphs where both fit 32 bits)
+  uint32_t col_bits;        // bits of the neighbour id in an adjp word
   const uint32_t* dnode;    // [n] Delta_node(v) = min incident weight (UINT32_MAX if isolated)
   // Optional relabeling (graph prep orders vertices by decreasing degree so
   // the state of high-degree vertices is contiguous).  Internal ids are
@@ -100,6 +102,9 @@ cudaError_t batched_occupancy(int dist_bits, int team, int* blocks_per_sm);
 // Graph preparation and small helpers (bc_prep.cu).
 cudaError_t launch_prep(uint32_t n, uint64_t nnz, const uint64_t* row_ptr, const uint32_t* col, const uint32_t* w,
                         uint2* adj, uint32_t* dnode, cudaStream_t st);
+// Packed form: adjp[e] = col[e] | w[e] << col_bits (caller checked that both fit).
+cudaError_t launch_pack32(uint64_t nnz, const uint32_t* col, const uint32_t* w, uint32_t col_bits, uint32_t* adjp,
+                          cudaStream_t st);
 cudaError_t launch_fill_u64(uint64_t* p, uint64_t count, uint64_t value, cudaStream_t st);
 cudaError_t launch_scale(double* p, uint64_t count, double scale, cudaStream_t st);
 cudaError_t launch_check_sources(const uint32_t* src, uint32_t k, uint32_t n, int* err, cudaStream_t st);

@@ -196,6 +196,7 @@ extern "C" int bc_compute_noalloc(const uint64_t* d_row_ptr, const uint32_t* d_c
     a.g.nnz = nnz;
     a.g.row_ptr = d_row_ptr;
     a.g.adj = adj;
+    a.g.adjp = nullptr;
     a.g.dnode = dnode;
     a.sources = d_sources;
     a.k = k;

@@ -103,7 +103,8 @@ __global__ void expand_kernel(GraphDev g, D* d, double* sig, const uint32_t* S, 
     const D dv = ldcg(&d[v]);
     double acc = 0.0;
     for (uint64_t e = g.row_ptr[v] + lane; e < g.row_ptr[v + 1]; e += 32) {
-      const uint2 ent = g.adj[e];
+      const uint2 ent = g.adjp ? make_uint2(g.adjp[e] & ((1u << g.col_bits) - 1u), g.adjp[e] >> g.col_bits)
+                                     : g.adj[e];
       const uint32_t u = ent.x;
       const D w = (D)ent.y;
       const D du = ldcg(&d[u]);
@@ -209,7 +210,8 @@ __global__ void backward_kernel(GraphDev g, const D* d, double* sig, const uint3
     const D dv = d[v];
     double acc = 0.0;
     for (uint64_t e = g.row_ptr[v] + lane; e < g.row_ptr[v + 1]; e += 32) {
-      const uint2 ent = g.adj[e];
+      const uint2 ent = g.adjp ? make_uint2(g.adjp[e] & ((1u << g.col_bits) - 1u), g.adjp[e] >> g.col_bits)
+                                     : g.adj[e];
       const D du = d[ent.x];
       if (du != INF && du == dv + (D)ent.y) acc += sig[ent.x];
     }

@@ -20,6 +20,12 @@ __global__ void pack_adj_kernel(uint64_t nnz, const uint32_t* __restrict__ col, 
     adj[e] = make_uint2(col[e], w[e]);
 }
 
+__global__ void pack32_kernel(uint64_t nnz, const uint32_t* __restrict__ col, const uint32_t* __restrict__ w,
+                              uint32_t col_bits, uint32_t* __restrict__ adjp) {
+  for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < nnz; e += (uint64_t)gridDim.x * blockDim.x)
+    adjp[e] = col[e] | (w[e] << col_bits);
+}
+
 __global__ void dnode_kernel(uint32_t n, const uint64_t* __restrict__ row_ptr, const uint32_t* __restrict__ w,
                              uint32_t* __restrict__ dnode) {
   const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
@@ -69,8 +75,15 @@ int grid_for(uint64_t work, int block) {
 
 cudaError_t launch_prep(uint32_t n, uint64_t nnz, const uint64_t* row_ptr, const uint32_t* col, const uint32_t* w,
                         uint2* adj, uint32_t* dnode, cudaStream_t st) {
-  if (nnz > 0) pack_adj_kernel<<<grid_for(nnz, 256), 256, 0, st>>>(nnz, col, w, adj);
+  if (nnz > 0 && adj) pack_adj_kernel<<<grid_for(nnz, 256), 256, 0, st>>>(nnz, col, w, adj);
   dnode_kernel<<<grid_for((uint64_t)n * 32, 256), 256, 0, st>>>(n, row_ptr, w, dnode);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack32(uint64_t nnz, const uint32_t* col, const uint32_t* w, uint32_t col_bits, uint32_t* adjp,
+                          cudaStream_t st) {
+  if (nnz == 0) return cudaSuccess;
+  pack32_kernel<<<grid_for(nnz, 256), 256, 0, st>>>(nnz, col, w, col_bits, adjp);
   return cudaGetLastError();
 }
 

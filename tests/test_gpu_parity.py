@@ -246,3 +246,18 @@ def test_dag_edge_list_overflow_falls_back_to_entry_scan():
         G.compute(np.arange(500, dtype=np.uint32), 1.0)
         st = G.stats()
         assert st.pair_overflows == 0 and st.dag_edges >= 499 * 500 * 0.9
+
+
+def test_wide_weights_use_unpacked_entries_and_64bit_distances():
+    rng = np.random.default_rng(55)
+    for i in range(10):
+        n = int(rng.integers(2, 200))
+        g = gen.random_small_graph(n, 0.1, 1, 2**31 - 1, rng)
+        src = np.arange(n, dtype=np.uint32)
+        with bc.Graph(g) as G:
+            if g.nnz:
+                assert G.info().dist_bits == 64
+            assert_bc_close(G.compute(src, 1.0), oracle.bc(g, src, 1.0))
+            d, sg, _ = G.sssp_debug(0)
+            d_ref, sg_ref, _ = oracle.sssp(g, 0)
+            assert np.array_equal(d, d_ref) and np.array_equal(sg, sg_ref)
