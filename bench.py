@@ -317,6 +317,9 @@ def main():
     ap.add_argument("--autotune", type=int, default=-1,
                     help="probe sources for the autotuner (-1: automatic size, 0: off)")
     ap.add_argument("--requests", type=int, default=2000, help="serving workload: number of requests")
+    ap.add_argument("--sources", type=int, default=0,
+                    help="use only the first K sources of the workload (small profiling cases); 0 = all")
+    ap.add_argument("--max-slots", type=int, default=0, help="cap on sources in flight (0 = automatic)")
     args = ap.parse_args()
 
     desc, maker = WORKLOADS[args.workload]
@@ -327,6 +330,9 @@ def main():
             run_serving(args, desc)
         return
     g, sources, scale = maker()
+    if args.sources:
+        scale = scale * len(sources) / min(args.sources, len(sources))
+        sources = sources[: args.sources]
     m = g.m
 
     ws, rank, local = dist_env()
@@ -350,6 +356,8 @@ def main():
             dist.barrier()
 
     dev = torch.device("cuda", local)
+    if args.max_slots:
+        bc.bc_set_config(max_slots=args.max_slots)
     G = bc.Graph(g)
     probe = args.autotune if args.autotune >= 0 else min(len(sources), 2048)
     tune_s = 0.0

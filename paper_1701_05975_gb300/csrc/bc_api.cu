@@ -330,6 +330,9 @@ BatchArgs make_args(bc_graph* g, Workspace* w, const RunCfg& r, const uint32_t* 
   a.debug_out = w->ctl->debug;
   a.warp_deg = r.warp_deg;
   a.team_deg = r.team_deg;
+  // the highest-degree vertices after relabeling: 128 KiB of 32-bit distance
+  // words per source (the whole L2 holds this prefix for ~1000 sources)
+  a.hot_n = g->relabeled ? std::min<uint32_t>(g->n, 32768u) : 0u;
   return a;
 }
 

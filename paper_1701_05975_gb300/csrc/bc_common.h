@@ -90,6 +90,7 @@ struct BatchArgs {
   unsigned long long* stats;  // [STAT_COUNT] or nullptr
   uint32_t warp_deg;   // forward expansion: rows with >= warp_deg entries get a warp each
   uint32_t team_deg;   // ... and rows with >= team_deg entries the whole team
+  uint32_t hot_n;      // ids below hot_n are gathered with an L2 evict-last hint
   uint32_t flags;      // RUN_*
   uint32_t* debug_out; // RUN_FORWARD_ONLY: [0] = levels, [1] = reached
 };
