@@ -313,7 +313,8 @@ def main():
     ap.add_argument("--workload", default="rmat20", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--plain-sample", type=int, default=0, help="also time the plain form on this many sources")
+    ap.add_argument("--plain-sample", type=int, default=16,
+                    help="also time the plain one-source-at-a-time form on this many sources (0: skip)")
     ap.add_argument("--autotune", type=int, default=-1,
                     help="probe sources for the autotuner (-1: automatic size, 0: off)")
     ap.add_argument("--requests", type=int, default=2000, help="serving workload: number of requests")
