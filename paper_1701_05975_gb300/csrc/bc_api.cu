@@ -78,6 +78,8 @@ SlabLayout make_layout(uint32_t n, int dist_bits) {
   off += align256((uint64_t)n * 4);
   L.off_far = off;
   off += align256((uint64_t)n * 4);
+  L.off_far2 = off;
+  off += align256((uint64_t)n * 4);
   L.off_acc = off;
   off += align256((uint64_t)n * 8);
   L.off_pend = off;

@@ -38,6 +38,8 @@ constexpr uint32_t NONE = 0xffffffffu;
 #define BCGPU_UNROLL 4
 #endif
 constexpr int UNROLL = BCGPU_UNROLL;  // independent edge loads in flight per thread
+constexpr int NEAR_REGS = 4;          // near-queue entries per thread kept in registers
+constexpr uint64_t FAR_LEVELS = 16;   // the second far level starts FAR_LEVELS split widths out
 
 template <typename D>
 __device__ __forceinline__ D dinf() {
@@ -91,10 +93,10 @@ __device__ __forceinline__ D dmin(D a, D b) {
 template <typename D, int TEAM>
 struct TeamShared {
   uint32_t src_idx;
-  uint32_t near_len, far_len, S_len, nlev;
+  uint32_t near_len, far_len, far2_len, S_len, nlev;
   uint32_t pair_len, pair_over;
   int stop;
-  D split;
+  D split, split2;  // near < split <= far < split2 <= far2
   uint32_t off[TEAM + 1];
   uint32_t vtx[TEAM];
   unsigned long long rs[TEAM];
@@ -307,6 +309,7 @@ struct Slab {
   uint32_t* ends;
   uint32_t* nearq;
   uint32_t* farq;
+  uint32_t* farq2;
   double* bacc;     // backward accumulator: sum of successor coefficients
   uint32_t* pend;   // pend[l] = end of level l's DAG edges in pairs
   uint2* pairs;     // DAG edges {predecessor u, vertex v}
@@ -323,6 +326,7 @@ __device__ __forceinline__ Slab<D> slab_at(const BatchArgs& a, uint32_t slot) {
   s.ends = reinterpret_cast<uint32_t*>(base + a.lay.off_ends);
   s.nearq = reinterpret_cast<uint32_t*>(base + a.lay.off_near);
   s.farq = reinterpret_cast<uint32_t*>(base + a.lay.off_far);
+  s.farq2 = reinterpret_cast<uint32_t*>(base + a.lay.off_far2);
   s.bacc = reinterpret_cast<double*>(base + a.lay.off_acc);
   s.pend = reinterpret_cast<uint32_t*>(base + a.lay.off_pend);
   s.pairs = reinterpret_cast<uint2*>(base + a.lay.off_pairs);
@@ -387,14 +391,17 @@ __device__ __forceinline__ void visit_entry(const Slab<D>& sl, TeamShared<D, TEA
       ++relax;
       const D old = atomic_min_d(&sl.d[u], nd);
       if (nd < old) {
-        if (old == INF) {
-          if (nd < split) {
-            sl.nearq[atomicAdd(&sh.near_len, 1u)] = u;
-          } else {
-            sl.farq[atomicAdd(&sh.far_len, 1u)] = u;
+        // first touch: queue by range; a later drop across a boundary
+        // queues u again in the lower range (the older entry goes stale)
+        if (nd < split) {
+          if (old >= split) sl.nearq[atomicAdd(&sh.near_len, 1u)] = u;
+        } else {
+          const D split2 = sh.split2;
+          if (nd < split2) {
+            if (old >= split2) sl.farq[atomicAdd(&sh.far_len, 1u)] = u;
+          } else if (old == INF) {
+            sl.farq2[atomicAdd(&sh.far2_len, 1u)] = u;
           }
-        } else if (old >= split && nd < split) {
-          sl.nearq[atomicAdd(&sh.near_len, 1u)] = u;
         }
       }
     }
@@ -627,12 +634,14 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
     sl.ends[1] = 1;
     sh.near_len = 0;
     sh.far_len = 0;
+    sh.far2_len = 0;
     sh.S_len = 1;
     sh.nlev = 1;
     sh.pair_len = 0;
     sh.pair_over = 0;
     sh.stop = 0;
     sh.split = sat_add<D>((D)0, a.width);
+    sh.split2 = sat_add<D>((D)0, (uint64_t)FAR_LEVELS * a.width);
   }
   team_sync<TEAM>();
   uint32_t f0 = 0, f1 = 1;
@@ -644,9 +653,54 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
     if (t == 0) sl.pend[sh.nlev - 1] = sh.pair_len;
     cyc_expand += clock64() - c0;
     c0 = clock64();
-    // refill the near queue from the far queue when it runs dry
-    while (sh.near_len == 0 && sh.far_len > 0) {
+    // refill the near queue from the far queue when it runs dry, and the far
+    // queue from the second far level when that runs dry too
+    while (sh.near_len == 0 && (sh.far_len > 0 || sh.far2_len > 0)) {
+      if (sh.far_len == 0) {
+        // every vertex below split2 is settled: split moves up to split2
+        const D old2 = sh.split2;
+        const uint32_t fl2 = sh.far2_len;
+        far_sc += 2ull * fl2;
+        D lo = INF, dummy = INF;
+        for (uint32_t base = 0; base < fl2; base += TEAM) {
+          const uint32_t j = base + t;
+          if (j < fl2) {
+            const D du = ldcg(&sl.d[ldcg(&sl.farq2[j])]);
+            if (du >= old2) lo = dmin(lo, du);
+          }
+        }
+        team_min2<D, TEAM>(lo, dummy, sh.red);
+        const D ns2 = (lo == INF) ? old2 : sat_add<D>(lo, (uint64_t)FAR_LEVELS * a.width);
+        uint32_t kept = 0;
+        for (uint32_t base = 0; base < fl2; base += TEAM) {
+          const uint32_t j = base + t;
+          uint32_t u = 0, keep = 0;
+          if (j < fl2) {
+            u = ldcg(&sl.farq2[j]);
+            const D du = ldcg(&sl.d[u]);
+            if (du >= old2) {  // below old2: queued again in a lower range already
+              if (du < ns2) sl.farq[atomicAdd(&sh.far_len, 1u)] = u;
+              else keep = 1;
+            }
+          }
+          uint32_t ktot;
+          const uint32_t kx = team_excl_scan<TEAM>(keep, &ktot, sh.scan);
+          if (TEAM == 32) __syncwarp();
+          if (keep) sl.farq2[kept + kx] = u;
+          kept += ktot;
+        }
+        team_sync<TEAM>();
+        if (t == 0) {
+          sh.far2_len = kept;
+          sh.split = old2;
+          sh.split2 = ns2;
+        }
+        ++refills;
+        team_sync<TEAM>();
+        continue;
+      }
       const D old = sh.split;
+      const D cap = sh.split2;
       const uint32_t fl = sh.far_len;
       far_sc += 2ull * fl;
       D lo = INF, dummy = INF;
@@ -658,7 +712,7 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
         }
       }
       team_min2<D, TEAM>(lo, dummy, sh.red);
-      const D ns = (lo == INF) ? old : sat_add<D>(lo, a.width);
+      const D ns = (lo == INF) ? old : dmin(sat_add<D>(lo, a.width), cap);
       uint32_t kept = 0;
       for (uint32_t base = 0; base < fl; base += TEAM) {
         const uint32_t j = base + t;
@@ -695,40 +749,79 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
     if (sh.stop || sh.near_len == 0) break;
     // threshold: Delta' = min(min_near (D + Delta_node), split) <= Delta_i
     const uint32_t nl = sh.near_len;
-    near_sc += 2ull * nl;
     const D split = sh.split;
-    D out = INF, dm = INF;
-    for (uint32_t base = 0; base < nl; base += TEAM) {
-      const uint32_t j = base + t;
-      if (j < nl) {
-        const uint32_t u = ldcg(&sl.nearq[j]);
-        const D du = ldcg(&sl.d[u]);
-        out = dmin(out, (D)(du + (D)__ldg(&a.g.dnode[u])));
-        dm = dmin(dm, du);
-      }
-    }
-    team_min2<D, TEAM>(out, dm, sh.red);
-    const D thr = dmin(out, split);
-    // settle (strict) and compact the near queue in place
     const uint32_t S0 = sh.S_len;
     uint32_t nset = 0, kept = 0;
-    for (uint32_t base = 0; base < nl; base += TEAM) {
-      const uint32_t j = base + t;
-      uint32_t u = 0, take = 0, valid = j < nl;
-      if (valid) {
-        u = ldcg(&sl.nearq[j]);
-        const D du = ldcg(&sl.d[u]);
-        take = du < thr;
-        if (a.settle_in && !take) take = du < (D)(dm + (D)__ldg(&a.g.dnode[u]));
+    if (nl <= TEAM * NEAR_REGS) {
+      // the whole near queue fits in registers: one gather pass
+      near_sc += nl;
+      uint32_t uu[NEAR_REGS];
+      D dd[NEAR_REGS], dn[NEAR_REGS];
+      D out = INF, dm = INF;
+#pragma unroll
+      for (int r = 0; r < NEAR_REGS; ++r) {
+        const uint32_t j = r * TEAM + t;
+        uu[r] = 0;
+        dd[r] = INF;
+        dn[r] = 0;
+        if (j < nl) {
+          uu[r] = ldcg(&sl.nearq[j]);
+          dd[r] = ldcg(&sl.d[uu[r]]);
+          dn[r] = (D)__ldg(&a.g.dnode[uu[r]]);
+          out = dmin(out, (D)(dd[r] + dn[r]));
+          dm = dmin(dm, dd[r]);
+        }
       }
-      uint32_t stot;
-      const uint32_t sx = team_excl_scan<TEAM>(take, &stot, sh.scan);
-      if (TEAM == 32) __syncwarp();
-      if (take) sl.S[S0 + nset + sx] = u;
-      if (valid && !take) sl.nearq[kept + (j - base) - sx] = u;
-      const uint32_t ccount = min((uint32_t)TEAM, nl - base);
-      nset += stot;
-      kept += ccount - stot;
+      team_min2<D, TEAM>(out, dm, sh.red);
+      const D thr = dmin(out, split);
+#pragma unroll
+      for (int r = 0; r < NEAR_REGS; ++r) {
+        const uint32_t base = r * TEAM;
+        if (base >= nl) break;  // uniform over the team
+        const uint32_t j = base + t;
+        const uint32_t valid = j < nl;
+        uint32_t take = valid && dd[r] < thr;
+        if (valid && a.settle_in && !take) take = dd[r] < (D)(dm + dn[r]);
+        uint32_t stot;
+        const uint32_t sx = team_excl_scan<TEAM>(take, &stot, sh.scan);
+        if (take) sl.S[S0 + nset + sx] = uu[r];
+        if (valid && !take) sl.nearq[kept + (j - base) - sx] = uu[r];
+        nset += stot;
+        kept += min((uint32_t)TEAM, nl - base) - stot;
+      }
+    } else {
+      near_sc += 2ull * nl;
+      D out = INF, dm = INF;
+      for (uint32_t base = 0; base < nl; base += TEAM) {
+        const uint32_t j = base + t;
+        if (j < nl) {
+          const uint32_t u = ldcg(&sl.nearq[j]);
+          const D du = ldcg(&sl.d[u]);
+          out = dmin(out, (D)(du + (D)__ldg(&a.g.dnode[u])));
+          dm = dmin(dm, du);
+        }
+      }
+      team_min2<D, TEAM>(out, dm, sh.red);
+      const D thr = dmin(out, split);
+      // settle (strict) and compact the near queue in place
+      for (uint32_t base = 0; base < nl; base += TEAM) {
+        const uint32_t j = base + t;
+        uint32_t u = 0, take = 0, valid = j < nl;
+        if (valid) {
+          u = ldcg(&sl.nearq[j]);
+          const D du = ldcg(&sl.d[u]);
+          take = du < thr;
+          if (a.settle_in && !take) take = du < (D)(dm + (D)__ldg(&a.g.dnode[u]));
+        }
+        uint32_t stot;
+        const uint32_t sx = team_excl_scan<TEAM>(take, &stot, sh.scan);
+        if (TEAM == 32) __syncwarp();
+        if (take) sl.S[S0 + nset + sx] = u;
+        if (valid && !take) sl.nearq[kept + (j - base) - sx] = u;
+        const uint32_t ccount = min((uint32_t)TEAM, nl - base);
+        nset += stot;
+        kept += ccount - stot;
+      }
     }
     ++phases;
     team_sync<TEAM>();
@@ -749,10 +842,11 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
   if (failed) {
     if (t == 0) atomicCAS(a.err, DEV_OK, DEV_ERR_TIMEOUT);
     // every touched vertex is settled (S), near or far: restore d = INF there
-    const uint32_t sl_n = sh.S_len, nl_n = sh.near_len, fl_n = sh.far_len;
+    const uint32_t sl_n = sh.S_len, nl_n = sh.near_len, fl_n = sh.far_len, fl2_n = sh.far2_len;
     for (uint32_t j = t; j < sl_n; j += TEAM) sl.d[ldcg(&sl.S[j])] = INF;
     for (uint32_t j = t; j < nl_n; j += TEAM) sl.d[ldcg(&sl.nearq[j])] = INF;
     for (uint32_t j = t; j < fl_n; j += TEAM) sl.d[ldcg(&sl.farq[j])] = INF;
+    for (uint32_t j = t; j < fl2_n; j += TEAM) sl.d[ldcg(&sl.farq2[j])] = INF;
   } else if (a.flags & RUN_FORWARD_ONLY) {
     if (t == 0 && a.debug_out) {
       a.debug_out[0] = sh.nlev;

@@ -31,8 +31,8 @@ struct GraphDev {
 // in flight).  d: distances (all INF between sources), sig: sigma during the
 // forward pass and the coefficient c = (1 + delta) / sigma during the backward
 // pass, S: settle order (the level lists of Algorithm 1's S/ends), ends: level
-// boundaries, nearq / farq: candidate queues (reached, unsettled vertices
-// below / at or above the current split).
+// boundaries, nearq / farq / farq2: candidate queues (reached, unsettled
+// vertices below the split, between the split and split2, above split2).
 // acc: per-vertex sum of successor coefficients during the backward pass
 // (zero between sources); pend: end of each level's range in the DAG edge
 // list; pairs: the shortest-path DAG edges (u -> v) found while pulling sigma,
@@ -40,7 +40,7 @@ struct GraphDev {
 // back to scanning every CSR entry).
 struct SlabLayout {
   uint64_t stride;
-  uint64_t off_d, off_sig, off_S, off_ends, off_near, off_far, off_acc, off_pend, off_pairs;
+  uint64_t off_d, off_sig, off_S, off_ends, off_near, off_far, off_far2, off_acc, off_pend, off_pairs;
   uint32_t pair_cap;
 };
 

@@ -68,6 +68,8 @@ SlabLayout na_layout(uint32_t n) {
   off += al256((uint64_t)n * 4);
   L.off_far = off;
   off += al256((uint64_t)n * 4);
+  L.off_far2 = off;
+  off += al256((uint64_t)n * 4);
   L.off_acc = off;
   off += al256((uint64_t)n * 8);
   L.off_pend = off;
