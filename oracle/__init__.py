@@ -48,9 +48,11 @@ def _bind(lib):
     lib.oracle_delta.argtypes = [ctypes.c_uint32, _u64p, _u32p, _u32p, ctypes.c_uint32, _f64p]
     lib.oracle_bc.argtypes = [ctypes.c_uint32, _u64p, _u32p, _u32p, _u32p, ctypes.c_uint32, ctypes.c_double, _f64p, ctypes.c_int]
     lib.oracle_edge_bc.argtypes = [ctypes.c_uint32, _u64p, _u32p, _u32p, _u32p, ctypes.c_uint32, ctypes.c_double, _f64p]
+    lib.oracle_bc_pull.argtypes = [ctypes.c_uint32, _u64p, _u32p, _u32p, _u32p, ctypes.c_uint32, ctypes.c_double, _f64p]
     lib.oracle_phased.argtypes = [ctypes.c_uint32, _u64p, _u32p, _u32p, ctypes.c_uint32, ctypes.c_int, ctypes.c_int,
                                   _u64p, _f64p, _u32p, _f64p, _u32p]
-    for f in (lib.oracle_sssp, lib.oracle_delta, lib.oracle_bc, lib.oracle_edge_bc, lib.oracle_phased):
+    for f in (lib.oracle_sssp, lib.oracle_delta, lib.oracle_bc, lib.oracle_edge_bc, lib.oracle_phased,
+              lib.oracle_bc_pull):
         f.restype = ctypes.c_int
     return lib
 
@@ -119,6 +121,18 @@ def bc(g, sources, scale: float = 1.0, nthreads: int = 1, lib=None):
     out = np.empty(g.n, np.float64)
     _check(lib.oracle_bc(g.n, _p(rp, _u64p), _p(col, _u32p), _p(w, _u32p), _p(src, _u32p) if len(src) else None,
                          len(src), scale, _p(out, _f64p), nthreads))
+    return out
+
+
+def bc_directed(g, sources, scale: float = 1.0, lib=None):
+    """BC on a directed CSR (rows are out-edges): dependencies pulled from
+    successors over out-edges (Algorithm 3's formula); also valid undirected."""
+    lib = lib or load()
+    rp, col, w = _csr(g)
+    src = np.ascontiguousarray(sources, dtype=np.uint32)
+    out = np.empty(g.n, np.float64)
+    _check(lib.oracle_bc_pull(g.n, _p(rp, _u64p), _p(col, _u32p), _p(w, _u32p), _p(src, _u32p) if len(src) else None,
+                              len(src), scale, _p(out, _f64p)))
     return out
 
 

@@ -314,6 +314,43 @@ int oracle_bc(uint32_t n, const uint64_t *row_ptr, const uint32_t *col, const ui
 }
 
 /* ------------------------------------------------------------------------ */
+/* Directed graphs (Sec. 2.1: the method extends to them).  Dependencies are */
+/* pulled from successors over out-edges, Algorithm 3's formula: walking the */
+/* settle order backwards, delta(a) = sum over entries (a -> b, w) with       */
+/* d(a) + w = d(b) of sigma_a / sigma_b * (1 + delta_b).  It needs no        */
+/* in-edges, so it is correct for any CSR, symmetric or not.                 */
+
+int oracle_bc_pull(uint32_t n, const uint64_t *row_ptr, const uint32_t *col, const uint32_t *w,
+                   const uint32_t *sources, uint32_t k, double scale, double *out_bc) {
+  int rc = check_csr(n, row_ptr, col, w);
+  if (rc) return rc;
+  for (uint32_t i = 0; i < k; ++i)
+    if (sources[i] >= n) return ORACLE_EINVAL;
+  for (uint32_t v = 0; v < n; ++v) out_bc[v] = 0.0;
+  work wk;
+  if (work_init(&wk, n)) { work_free(&wk); return ORACLE_ENOMEM; }
+  for (uint32_t i = 0; i < k; ++i) {
+    uint32_t s = sources[i];
+    int64_t settled = sssp_count(n, row_ptr, col, w, s, &wk);
+    if (settled < 0) { work_free(&wk); return ORACLE_ENOMEM; }
+    for (int64_t j = settled; j-- > 0;) {
+      uint32_t a = wk.S[j];
+      double dep = 0.0;
+      for (uint64_t e = row_ptr[a]; e < row_ptr[a + 1]; ++e) {
+        uint32_t b = col[e];
+        if (wk.d[b] != INF_DIST && wk.d[a] + (uint64_t)w[e] == wk.d[b])
+          dep += wk.sigma[a] / wk.sigma[b] * (1.0 + wk.delta[b]);
+      }
+      wk.delta[a] = dep;
+      if (a != s) out_bc[a] += dep;
+    }
+  }
+  work_free(&wk);
+  for (uint32_t v = 0; v < n; ++v) out_bc[v] *= scale;
+  return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Edge betweenness (the paper's tool reports node and edge BC, Sec. 1).    */
 /* Per CSR entry e = (a -> b, w): the pair-dependency share that crosses it  */
 /* in the direction a -> b, i.e. when a is a shortest-path predecessor of b  */

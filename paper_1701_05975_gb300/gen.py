@@ -209,6 +209,42 @@ def rmat_graph(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.
     return csr_from_undirected(n, u, v, w, name=f"rmat_s{scale}_ef{edge_factor}")
 
 
+def rmat_digraph(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19, c: float = 0.19,
+                 wmin: int = 1, wmax: int = 255, seed: int = 0) -> CSRGraph:
+    """Directed R-MAT: the same draws as rmat_graph, but every generated
+    (source, target) pair is kept as a directed edge (self-loops and repeated
+    pairs removed); one weight per directed edge."""
+    rng_e, rng_w, _, _ = _streams(seed)
+    n = 1 << scale
+    ne = edge_factor * n
+    src = np.zeros(ne, dtype=np.uint32)
+    dst = np.zeros(ne, dtype=np.uint32)
+    fa, fab, fabc = np.float32(a), np.float32(a + b), np.float32(a + b + c)
+    for bit in range(scale):
+        r = rng_e.random(ne, dtype=np.float32)
+        go_down = r >= fab
+        go_right = (r >= fa) ^ go_down ^ (r >= fabc)
+        src |= go_down.view(np.uint8).astype(np.uint32) << np.uint32(bit)
+        dst |= go_right.view(np.uint8).astype(np.uint32) << np.uint32(bit)
+    perm = rng_e.permutation(n).astype(np.int64)
+    s64 = perm[src.astype(np.int64)]
+    d64 = perm[dst.astype(np.int64)]
+    keep = s64 != d64
+    key = np.unique(s64[keep] * n + d64[keep])
+    u, v = key // n, key % n
+    w = rng_w.integers(wmin, wmax + 1, size=len(u), dtype=np.int64)
+    return csr_from_directed(n, u, v, w, name=f"rmat_dir_s{scale}_ef{edge_factor}")
+
+
+def random_small_digraph(n: int, p: float, wmin: int, wmax: int, rng: np.random.Generator) -> CSRGraph:
+    """Tiny directed G(n, p) (each ordered pair independently)."""
+    iu, ju = np.nonzero(~np.eye(n, dtype=bool))
+    keep = rng.random(len(iu)) < p
+    u, v = iu[keep], ju[keep]
+    w = rng.integers(wmin, wmax + 1, size=len(u))
+    return csr_from_directed(n, u, v, w, name=f"small_dir_n{n}")
+
+
 def grid_graph(rows: int, cols: int, remove: int | None = None, remove_frac: float = 0.05,
                wmin: int = 1, wmax: int = 10000, seed: int = 0) -> CSRGraph:
     """4-neighbour rows x cols lattice (vertex id = r * cols + c) with `remove`

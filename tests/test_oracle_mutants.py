@@ -28,6 +28,9 @@ MUTANTS = {
     "phased_nonstrict": ("                           : (U[v] && d[v] < Delta);", "                           : (U[v] && d[v] <= Delta);"),
     "phased_dnode_max": ("if ((uint64_t)w[e] < m) m = w[e];", "if (m == INF_DIST || (uint64_t)w[e] > m) m = w[e];"),
     "edge_share_wrong_dir": ("out_ebc[e] += share;", "out_ebc[e] += share * (wk.d[a] == 0 ? 2.0 : 1.0);"),
+    "pull_dropped_one_plus": ("dep += wk.sigma[a] / wk.sigma[b] * (1.0 + wk.delta[b]);",
+                              "dep += wk.sigma[a] / wk.sigma[b] * (wk.delta[b]);"),
+    "pull_source_counted": ("if (a != s) out_bc[a] += dep;", "out_bc[a] += dep;"),
 }
 
 
@@ -38,6 +41,7 @@ def any_pin_fails(lib) -> bool:
         lambda: _closed_forms(lib),
         lambda: _fig1a(lib),
         lambda: _phased_vs_brandes(lib),
+        lambda: _directed(lib),
     ]
     for c in checks:
         try:
@@ -60,6 +64,15 @@ def _fig1a(lib):
     for crit, order, want in expects:
         _, sg, _, _, _ = oracle.phased(g, s, nonstrict=(crit == "nonstrict"), reverse=(order == "reverse"), lib=lib)
         assert sg[3] == want
+
+
+def _directed(lib):
+    rng = np.random.default_rng(44)
+    for _ in range(30):
+        n = int(rng.integers(2, 6))
+        g = gen.random_small_digraph(n, 0.5, 1, 3, rng)
+        _, _, bc_ref, _ = pins.brute_force(g)
+        pins.close(oracle.bc_directed(g, np.arange(n), 1.0, lib=lib), [float(x) for x in bc_ref])
 
 
 def _phased_vs_brandes(lib):

@@ -365,3 +365,54 @@ def test_invalid_inputs_rejected():
     bad.col[0] = 7
     with pytest.raises(oracle.OracleError):
         oracle.sssp(bad, 0)
+
+
+# ---------------------------------------------------------------------------
+# directed graphs (Sec. 2.1: the method extends to them)
+
+
+def test_directed_brute_force_small_graphs():
+    rng = np.random.default_rng(61)
+    for _ in range(150):
+        n = int(rng.integers(1, 7))
+        g = gen.random_small_digraph(n, float(rng.choice([0.2, 0.4, 0.7])), 1, 3, rng)
+        dist, sigma, bc_ref, ebc_ref = brute_force(g)
+        for s in range(g.n):
+            d, sg, _ = oracle.sssp(g, s)
+            want_d = np.array([U64MAX if x == float("inf") else int(x) for x in dist[s]], dtype=np.uint64)
+            assert np.array_equal(d, want_d)
+            assert np.array_equal(sg, np.array(sigma[s], dtype=np.float64))
+        allsrc = np.arange(g.n, dtype=np.uint32)
+        close(oracle.bc_directed(g, allsrc, 1.0), [float(x) for x in bc_ref])
+        close(oracle.edge_bc(g, allsrc, 1.0), [float(x) for x in ebc_ref])
+
+
+def test_directed_closed_forms():
+    # directed path: v_i is interior to i * (n - 1 - i) ordered pairs
+    for n in (2, 5, 9):
+        g = gen.csr_from_directed(n, np.arange(n - 1), np.arange(1, n), np.full(n - 1, 3))
+        assert np.array_equal(oracle.bc_directed(g, np.arange(n), 1.0), [i * (n - 1 - i) for i in range(n)])
+    # directed unit cycle: every vertex (n - 1)(n - 2) / 2
+    for n in (3, 4, 7):
+        g = gen.csr_from_directed(n, np.arange(n), (np.arange(n) + 1) % n, np.ones(n))
+        np.testing.assert_allclose(oracle.bc_directed(g, np.arange(n), 1.0), (n - 1) * (n - 2) / 2)
+
+
+def test_pull_and_push_accumulation_agree_on_undirected_graphs():
+    for g in [gen.er_graph(200, 900, 1, 6, seed=71), gen.ba_graph(300, 3, 1, 4, seed=72)]:
+        src = np.arange(g.n, dtype=np.uint32)
+        np.testing.assert_allclose(oracle.bc_directed(g, src, 0.5), oracle.bc(g, src, 0.5), rtol=1e-12, atol=0)
+
+
+def test_directed_networkx_cross_check():
+    nx = pytest.importorskip("networkx")
+    rng = np.random.default_rng(73)
+    g = gen.random_small_digraph(120, 0.05, 1, 9, rng)
+    G = nx.DiGraph()
+    G.add_nodes_from(range(g.n))
+    rows, cols, ws = g.edges()
+    for a, b, w in zip(rows.tolist(), cols.tolist(), ws.tolist()):
+        G.add_edge(a, b, weight=w)
+    ref = nx.betweenness_centrality(G, weight="weight", normalized=False)
+    got = oracle.bc_directed(g, np.arange(g.n), 1.0)
+    np.testing.assert_allclose(got, [ref[v] for v in range(g.n)], rtol=1e-9, atol=1e-9)
