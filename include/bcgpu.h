@@ -57,6 +57,10 @@ extern "C" {
 #define BC_RELABEL_DEGREE 0x2u   /* always store vertices internally in decreasing-degree order */
 #define BC_KEEP_ORDER 0x4u       /* never relabel (default: relabel when the top 1% of vertices by degree
                                     hold more than 10% of the CSR entries) */
+#define BC_DIRECTED 0x8u         /* the CSR rows are out-edges of a directed graph (Sec. 2.1: the method
+                                    extends to directed graphs); no symmetry is assumed.  Distances and
+                                    sigma follow out-edges; BC counts ordered pairs (use scale 1).  The
+                                    batched path only (BC_MODE_PLAIN and bc_compute_noalloc are undirected). */
 
 /* ---- execution modes --------------------------------------------------- */
 #define BC_MODE_BATCHED 0u /* persistent launch: one team (warp or CTA) per source, many sources in flight */
@@ -123,6 +127,7 @@ typedef struct bc_graph_info {
   uint64_t device_bytes;  /* resident CSR + per-vertex graph data */
   uint64_t slab_bytes;    /* device bytes one in-flight source needs */
   uint32_t relabeled;     /* 1 when vertices are stored internally in decreasing-degree order */
+  uint32_t directed;      /* 1 for a BC_DIRECTED graph */
 } bc_graph_info;
 
 int bc_graph_get_info(bc_graph_t g, bc_graph_info *out);

@@ -29,6 +29,7 @@ BC_ERR_CANCELLED = 6
 BC_UNDIRECTED_CHECK = 1
 BC_RELABEL_DEGREE = 2
 BC_KEEP_ORDER = 4
+BC_DIRECTED = 8
 BC_MODE_BATCHED = 0
 BC_MODE_PLAIN = 1
 BC_REQ_QUEUED, BC_REQ_RUNNING, BC_REQ_DONE, BC_REQ_FAILED, BC_REQ_CANCELLED = range(5)
@@ -52,7 +53,7 @@ class bc_config(ctypes.Structure):
 class bc_graph_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint32), ("nnz", ctypes.c_uint64), ("max_weight", ctypes.c_uint32),
                 ("dist_bits", ctypes.c_uint32), ("device_bytes", ctypes.c_uint64), ("slab_bytes", ctypes.c_uint64),
-                ("relabeled", ctypes.c_uint32)]
+                ("relabeled", ctypes.c_uint32), ("directed", ctypes.c_uint32)]
 
 
 class bc_run_stats(ctypes.Structure):

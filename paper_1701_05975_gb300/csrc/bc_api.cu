@@ -147,6 +147,11 @@ struct bc_graph {
   uint32_t* dnode = nullptr;
   double* ebc = nullptr;  // lazily allocated [nnz]
   bool relabeled = false;
+  bool directed = false;
+  uint64_t* in_row_ptr = nullptr;  // directed graphs: in-edge CSR (same entry form)
+  uint2* in_adj = nullptr;
+  uint32_t* in_adjp = nullptr;
+  uint32_t* dnode_in = nullptr;
   uint32_t* o2n = nullptr;  // device maps (relabeled graphs only)
   uint32_t* n2o = nullptr;
   uint32_t* e2o = nullptr;
@@ -177,6 +182,10 @@ GraphDev view(const bc_graph* g) {
   v.o2n = g->o2n;
   v.n2o = g->n2o;
   v.e2o = g->e2o;
+  v.in_row_ptr = g->in_row_ptr;
+  v.in_adj = g->in_adj;
+  v.in_adjp = g->in_adjp;
+  v.dnode_in = g->dnode_in;
   return v;
 }
 
@@ -437,6 +446,7 @@ int compute_sync(bc_graph* g, const uint32_t* sources, uint32_t k, double scale,
 }
 
 int compute_plain(bc_graph* g, const uint32_t* sources, uint32_t k, double scale, double* out_bc, const RunCfg& r) {
+  if (g->directed) return fail(BC_ERR_INVALID, "BC_MODE_PLAIN runs undirected graphs only");
   for (uint32_t i = 0; i < k; ++i)
     if (sources[i] >= g->n) return fail(BC_ERR_INVALID, "source %u out of range (n = %u)", sources[i], g->n);
   cudaStream_t st = g->stream;
@@ -614,6 +624,9 @@ int bc_graph_create(const uint64_t* row_ptr, const uint32_t* col_idx, const uint
     if (w[e] == 0) return fail(BC_ERR_INVALID, "weight 0 at entry %llu", (unsigned long long)e);
     max_w = std::max(max_w, w[e]);
   }
+  const bool directed = (flags & BC_DIRECTED) != 0;
+  if (directed && (flags & BC_UNDIRECTED_CHECK))
+    return fail(BC_ERR_INVALID, "BC_DIRECTED and BC_UNDIRECTED_CHECK exclude each other");
   if (flags & BC_UNDIRECTED_CHECK) {
     std::vector<std::array<uint32_t, 3>> a, b;
     a.reserve(nnz);
@@ -630,25 +643,27 @@ int bc_graph_create(const uint64_t* row_ptr, const uint32_t* col_idx, const uint
   // Layout: optionally renumber vertices by decreasing degree (stable), so
   // the per-source state of the vertices most edges point at is contiguous.
   bool relabel = false;
+  // degree used for ordering: out-degree, plus in-degree for directed graphs
+  std::vector<uint64_t> tdeg(n);
+  for (uint32_t v = 0; v < n; ++v) tdeg[v] = row_ptr[v + 1] - row_ptr[v];
+  if (directed)
+    for (uint64_t e = 0; e < nnz; ++e) ++tdeg[col_idx[e]];
   if (flags & BC_RELABEL_DEGREE) {
     relabel = true;
   } else if (!(flags & BC_KEEP_ORDER) && n >= 1024) {
-    std::vector<uint64_t> degs(n);
-    for (uint32_t v = 0; v < n; ++v) degs[v] = row_ptr[v + 1] - row_ptr[v];
+    std::vector<uint64_t> degs(tdeg);
     const size_t top = std::max<size_t>(1, n / 100);
     std::nth_element(degs.begin(), degs.begin() + top, degs.end(), std::greater<uint64_t>());
     uint64_t top_sum = 0;
     for (size_t i = 0; i < top; ++i) top_sum += degs[i];
-    relabel = nnz > 0 && (double)top_sum > 0.10 * (double)nnz;
+    relabel = nnz > 0 && (double)top_sum > (directed ? 0.20 : 0.10) * (double)nnz;
   }
   std::vector<uint64_t> rp2;
   std::vector<uint32_t> col2, w2, n2o, o2n, e2o;
   if (relabel) {
     n2o.resize(n);
     for (uint32_t v = 0; v < n; ++v) n2o[v] = v;
-    std::stable_sort(n2o.begin(), n2o.end(), [&](uint32_t a, uint32_t b) {
-      return row_ptr[a + 1] - row_ptr[a] > row_ptr[b + 1] - row_ptr[b];
-    });
+    std::stable_sort(n2o.begin(), n2o.end(), [&](uint32_t a, uint32_t b) { return tdeg[a] > tdeg[b]; });
     o2n.resize(n);
     for (uint32_t i = 0; i < n; ++i) o2n[n2o[i]] = i;
     rp2.resize((size_t)n + 1);
@@ -679,6 +694,23 @@ int bc_graph_create(const uint64_t* row_ptr, const uint32_t* col_idx, const uint
     row_ptr = rp2.data();
     col_idx = col2.data();
     w = w2.data();
+  }
+  // directed: the in-edge CSR (transpose), each row sorted by source id
+  std::vector<uint64_t> irp;
+  std::vector<uint32_t> icol, iw;
+  if (directed) {
+    irp.assign((size_t)n + 1, 0);
+    for (uint64_t e = 0; e < nnz; ++e) ++irp[(size_t)col_idx[e] + 1];
+    for (uint32_t v = 0; v < n; ++v) irp[v + 1] += irp[v];
+    std::vector<uint64_t> fill(irp.begin(), irp.end() - 1);
+    icol.resize(nnz);
+    iw.resize(nnz);
+    for (uint32_t v = 0; v < n; ++v)
+      for (uint64_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+        const uint64_t pos = fill[col_idx[e]]++;
+        icol[pos] = v;
+        iw[pos] = w[e];
+      }
   }
   auto g = std::make_unique<bc_graph>();
   CK(cudaGetDevice(&g->device));
@@ -726,6 +758,22 @@ int bc_graph_create(const uint64_t* row_ptr, const uint32_t* col_idx, const uint
   }
   if (e == cudaSuccess) e = launch_prep(n, nnz, g->row_ptr, d_col, d_w, g->adj, g->dnode, g->stream);
   if (e == cudaSuccess && packed) e = launch_pack32(nnz, d_col, d_w, col_bits, g->adjp, g->stream);
+  if (directed && e == cudaSuccess) {
+    // same entry form for the in-edge CSR; d_col / d_w are reused for it
+    g->directed = true;
+    e = cudaStreamSynchronize(g->stream);
+    if (e == cudaSuccess) e = cudaMalloc(&g->in_row_ptr, ((size_t)n + 1) * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&g->dnode_in, (size_t)n * 4);
+    if (e == cudaSuccess) {
+      if (packed) e = cudaMalloc(&g->in_adjp, std::max<size_t>(nnz, 1) * 4);
+      else e = cudaMalloc(&g->in_adj, std::max<size_t>(nnz, 1) * 8);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g->in_row_ptr, irp.data(), ((size_t)n + 1) * 8, cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(d_col, icol.data(), nnz * 4, cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(d_w, iw.data(), nnz * 4, cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess) e = launch_prep(n, nnz, g->in_row_ptr, d_col, d_w, g->in_adj, g->dnode_in, g->stream);
+    if (e == cudaSuccess && packed) e = launch_pack32(nnz, d_col, d_w, col_bits, g->in_adjp, g->stream);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
   cudaFree(d_col);
   cudaFree(d_w);
@@ -737,10 +785,14 @@ int bc_graph_create(const uint64_t* row_ptr, const uint32_t* col_idx, const uint
     cudaFree(g->o2n);
     cudaFree(g->n2o);
     cudaFree(g->e2o);
+    cudaFree(g->in_row_ptr);
+    cudaFree(g->in_adj);
+    cudaFree(g->in_adjp);
+    cudaFree(g->dnode_in);
     if (g->stream) cudaStreamDestroy(g->stream);
     return cuda_fail(e, "bc_graph_create upload");
   }
-  g->device_bytes = ((uint64_t)n + 1) * 8 + nnz * (packed ? 4 : 8) + (uint64_t)n * 4 +
+  g->device_bytes = (((uint64_t)n + 1) * 8 + nnz * (packed ? 4 : 8) + (uint64_t)n * 4) * (directed ? 2 : 1) +
                     (relabel ? 8ull * n + 4ull * nnz : 0);
   *out = g.release();
   return BC_OK;
@@ -765,6 +817,10 @@ int bc_graph_destroy(bc_graph_t g) {
   cudaFree(g->o2n);
   cudaFree(g->n2o);
   cudaFree(g->e2o);
+  cudaFree(g->in_row_ptr);
+  cudaFree(g->in_adj);
+  cudaFree(g->in_adjp);
+  cudaFree(g->dnode_in);
   cudaStreamDestroy(g->stream);
   delete g;
   return BC_OK;
@@ -780,6 +836,7 @@ int bc_graph_get_info(bc_graph_t g, bc_graph_info* out) {
   out->device_bytes = g->device_bytes;
   out->slab_bytes = make_layout(g->n, g->dist_bits).stride;
   out->relabeled = g->relabeled ? 1u : 0u;
+  out->directed = g->directed ? 1u : 0u;
   return BC_OK;
 }
 

@@ -90,6 +90,14 @@ __device__ __forceinline__ D dmin(D a, D b) {
   return a < b ? a : b;
 }
 
+// d + Delta_node for the OUT threshold (Eq. 2); a vertex without out-edges
+// (Delta_node = UINT32_MAX, only in directed graphs) cannot lower any
+// distance, so its term is +infinity.
+template <typename D>
+__device__ __forceinline__ D out_key(D d, uint32_t dnode) {
+  return dnode == 0xffffffffu ? dinf<D>() : (D)(d + (D)dnode);
+}
+
 template <typename D, int TEAM>
 struct TeamShared {
   uint32_t src_idx;
@@ -255,8 +263,19 @@ __device__ __forceinline__ uint64_t policy_evict_last() {
 
 // CSR entry e as {neighbour, weight}: from the packed 32-bit form
 // (neighbour | weight << col_bits) when PACKED, else from {col, w} records.
+// One CSR (the out-edges, or for directed graphs the in-edges) as a walk sees it.
+struct Rows {
+  const uint64_t* row_ptr;
+  const uint2* adj;
+  const uint32_t* adjp;
+  uint32_t col_bits;
+};
+
+__device__ __forceinline__ Rows out_rows(const GraphDev& g) { return Rows{g.row_ptr, g.adj, g.adjp, g.col_bits}; }
+__device__ __forceinline__ Rows in_rows(const GraphDev& g) { return Rows{g.in_row_ptr, g.in_adj, g.in_adjp, g.col_bits}; }
+
 template <bool PACKED>
-__device__ __forceinline__ uint2 load_entry(const GraphDev& g, uint64_t e, uint64_t pol) {
+__device__ __forceinline__ uint2 load_entry(const Rows& g, uint64_t e, uint64_t pol) {
 #if BCGPU_ADJ_HINT
   if constexpr (PACKED) {
     uint32_t x;
@@ -373,19 +392,24 @@ __device__ __forceinline__ uint32_t owner_of(const uint32_t* off, uint32_t cnt, 
 // One CSR entry {u, w} of chunk vertex i during the forward pass: if u is a
 // shortest-path predecessor (settled in an earlier batch), pull its sigma and
 // record the DAG edge u -> v; otherwise relax u.
-template <typename D, int TEAM>
+// Walk modes: an undirected row serves both the sigma pull and the
+// relaxation; a directed graph pulls over its in-edges and relaxes over its
+// out-edges in two walks.
+enum : int { WALK_BOTH = 0, WALK_PULL = 1, WALK_RELAX = 2 };
+
+template <typename D, int TEAM, int MODE>
 __device__ __forceinline__ void visit_entry(const Slab<D>& sl, TeamShared<D, TEAM>& sh, uint32_t i, uint2 ent, D du,
                                             D split, unsigned long long& relax) {
   const D INF = dinf<D>();
   const uint32_t u = ent.x;
   const D w = (D)ent.y;
   const D dvi = sh.dv[i];
-  if (du != INF && du + w == dvi) {
+  if (MODE != WALK_RELAX && du != INF && du + w == dvi) {
     atomicAdd(&sh.acc[i], ldg_slab(&sl.sig[u]));
     const uint32_t pos = atomicAdd(&sh.pair_len, 1u);
     if (pos < sl.pair_cap) sl.pairs[pos] = make_uint2(u, sh.vtx[i]);
     else sh.pair_over = 1;
-  } else {
+  } else if (MODE != WALK_PULL) {
     const D nd = dvi + w;
     if (nd < du) {
       ++relax;
@@ -410,9 +434,10 @@ __device__ __forceinline__ void visit_entry(const Slab<D>& sl, TeamShared<D, TEA
 
 // `lanes` threads (this one is number l) walk the whole row of chunk vertex i,
 // UNROLL independent adjacency loads and distance gathers in flight each.
-template <typename D, int TEAM, bool PACKED>
-__device__ __forceinline__ void walk_row(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, TEAM>& sh, uint32_t i,
-                                         uint32_t l, uint32_t lanes, D split, unsigned long long& relax) {
+template <typename D, int TEAM, bool PACKED, int MODE>
+__device__ __forceinline__ void walk_row(const BatchArgs& a, const Rows& rows, const Slab<D>& sl,
+                                         TeamShared<D, TEAM>& sh, uint32_t i, uint32_t l, uint32_t lanes, D split,
+                                         unsigned long long& relax) {
   const D INF = dinf<D>();
   const uint64_t r0 = sh.rs[i];
   const uint32_t deg = sh.dg[i];
@@ -422,14 +447,14 @@ __device__ __forceinline__ void walk_row(const BatchArgs& a, const Slab<D>& sl, 
 #pragma unroll
     for (int q = 0; q < UNROLL; ++q) {
       const uint32_t e = e0 + q * lanes;
-      ent[q] = e < deg ? load_entry<PACKED>(a.g, r0 + e, pf) : make_uint2(0, 0);
+      ent[q] = e < deg ? load_entry<PACKED>(rows, r0 + e, pf) : make_uint2(0, 0);
     }
     D dus[UNROLL];
 #pragma unroll
     for (int q = 0; q < UNROLL; ++q) dus[q] = (e0 + q * lanes < deg) ? gather_d(sl.d, ent[q].x, a.hot_n, pl) : INF;
 #pragma unroll
     for (int q = 0; q < UNROLL; ++q)
-      if (e0 + q * lanes < deg) visit_entry<D, TEAM>(sl, sh, i, ent[q], dus[q], split, relax);
+      if (e0 + q * lanes < deg) visit_entry<D, TEAM, MODE>(sl, sh, i, ent[q], dus[q], split, relax);
   }
 }
 
@@ -440,9 +465,9 @@ __device__ __forceinline__ void walk_row(const BatchArgs& a, const Slab<D>& sl, 
 // remaining short rows are spread edge by edge over all threads (a degree
 // scan plus a binary search for each edge's row).  No barrier separates the
 // tiers, so threads that finish one move on to the next.
-template <typename D, int TEAM, bool PACKED>
-__device__ void expand_forward(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, TEAM>& sh, uint32_t f0,
-                               uint32_t f1, uint32_t s, int t, D split, unsigned long long& relax,
+template <typename D, int TEAM, bool PACKED, int MODE>
+__device__ void expand_forward(const BatchArgs& a, const Rows& rows, const Slab<D>& sl, TeamShared<D, TEAM>& sh,
+                               uint32_t f0, uint32_t f1, uint32_t s, int t, D split, unsigned long long& relax,
                                unsigned long long& scanned) {
   const D INF = dinf<D>();
   const uint32_t warp_deg = a.warp_deg;
@@ -452,8 +477,8 @@ __device__ void expand_forward(const BatchArgs& a, const Slab<D>& sl, TeamShared
     uint32_t deg = 0, small = 0, is_w = 0, is_t = 0;
     if ((uint32_t)t < cnt) {
       const uint32_t v = ldcg(&sl.S[base + t]);
-      const uint64_t r0 = __ldg(&a.g.row_ptr[v]);
-      deg = (uint32_t)(__ldg(&a.g.row_ptr[v + 1]) - r0);
+      const uint64_t r0 = __ldg(&rows.row_ptr[v]);
+      deg = (uint32_t)(__ldg(&rows.row_ptr[v + 1]) - r0);
       sh.vtx[t] = v;
       sh.rs[t] = r0;
       sh.dg[t] = deg;
@@ -482,7 +507,7 @@ __device__ void expand_forward(const BatchArgs& a, const Slab<D>& sl, TeamShared
     for (uint32_t h = 0; h < nt; ++h) {
       const uint32_t i = sh.tlist[h];
       if (t == 0) scanned += sh.dg[i];
-      walk_row<D, TEAM, PACKED>(a, sl, sh, i, (uint32_t)t, TEAM, split, relax);
+      walk_row<D, TEAM, PACKED, MODE>(a, rows, sl, sh, i, (uint32_t)t, TEAM, split, relax);
     }
     // tier 2: one warp per row, rows taken in turn
     if constexpr (TEAM > 32) {
@@ -494,7 +519,7 @@ __device__ void expand_forward(const BatchArgs& a, const Slab<D>& sl, TeamShared
         if (wi >= nw) break;
         const uint32_t i = sh.wlist[wi];
         if (lane == 0) scanned += sh.dg[i];
-        walk_row<D, TEAM, PACKED>(a, sl, sh, i, lane, 32, split, relax);
+        walk_row<D, TEAM, PACKED, MODE>(a, rows, sl, sh, i, lane, 32, split, relax);
       }
     }
     // tier 1: short rows, edge-parallel over the whole team
@@ -509,7 +534,7 @@ __device__ void expand_forward(const BatchArgs& a, const Slab<D>& sl, TeamShared
         ent[q] = make_uint2(0, 0);
         if (e < total_small) {
           iv[q] = owner_of<TEAM>(sh.off, cnt, e);
-          ent[q] = load_entry<PACKED>(a.g, sh.rs[iv[q]] + (e - sh.off[iv[q]]), pf);
+          ent[q] = load_entry<PACKED>(rows, sh.rs[iv[q]] + (e - sh.off[iv[q]]), pf);
         }
       }
       D dus[UNROLL];
@@ -517,10 +542,10 @@ __device__ void expand_forward(const BatchArgs& a, const Slab<D>& sl, TeamShared
       for (int q = 0; q < UNROLL; ++q) dus[q] = (iv[q] != NONE) ? gather_d(sl.d, ent[q].x, a.hot_n, pl) : INF;
 #pragma unroll
       for (int q = 0; q < UNROLL; ++q)
-        if (iv[q] != NONE) visit_entry<D, TEAM>(sl, sh, iv[q], ent[q], dus[q], split, relax);
+        if (iv[q] != NONE) visit_entry<D, TEAM, MODE>(sl, sh, iv[q], ent[q], dus[q], split, relax);
     }
     team_sync<TEAM>();
-    if ((uint32_t)t < cnt && sh.vtx[t] != s) sl.sig[sh.vtx[t]] = sh.acc[t];
+    if (MODE != WALK_RELAX && (uint32_t)t < cnt && sh.vtx[t] != s) sl.sig[sh.vtx[t]] = sh.acc[t];
     team_sync<TEAM>();
   }
 }
@@ -548,7 +573,7 @@ __device__ void accumulate_level(const BatchArgs& a, const Slab<D>& sl, TeamShar
         if (e < total) {
           iv[q] = owner_of<TEAM>(sh.off, cnt, e);
           entry[q] = sh.rs[iv[q]] + (e - sh.off[iv[q]]);
-          ent[q] = load_entry<PACKED>(a.g, entry[q], policy_evict_first());
+          ent[q] = load_entry<PACKED>(out_rows(a.g), entry[q], policy_evict_first());
         }
       }
       D dus[UNROLL];
@@ -648,7 +673,13 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
   for (;;) {
     const D split0 = sh.split;
     c0 = clock64();
-    expand_forward<D, TEAM, PACKED>(a, sl, sh, f0, f1, s, t, split0, relax, scanned);
+    if (a.g.in_row_ptr) {
+      // directed: sigma from in-edges, then relax out-edges
+      expand_forward<D, TEAM, PACKED, WALK_PULL>(a, in_rows(a.g), sl, sh, f0, f1, s, t, split0, relax, scanned);
+      expand_forward<D, TEAM, PACKED, WALK_RELAX>(a, out_rows(a.g), sl, sh, f0, f1, s, t, split0, relax, scanned);
+    } else {
+      expand_forward<D, TEAM, PACKED, WALK_BOTH>(a, out_rows(a.g), sl, sh, f0, f1, s, t, split0, relax, scanned);
+    }
     // DAG edges into the batch just expanded end here
     if (t == 0) sl.pend[sh.nlev - 1] = sh.pair_len;
     cyc_expand += clock64() - c0;
@@ -756,7 +787,7 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
       // the whole near queue fits in registers: one gather pass
       near_sc += nl;
       uint32_t uu[NEAR_REGS];
-      D dd[NEAR_REGS], dn[NEAR_REGS];
+      D dd[NEAR_REGS], dn[NEAR_REGS], dni[NEAR_REGS];
       D out = INF, dm = INF;
 #pragma unroll
       for (int r = 0; r < NEAR_REGS; ++r) {
@@ -764,11 +795,13 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
         uu[r] = 0;
         dd[r] = INF;
         dn[r] = 0;
+        dni[r] = 0;
         if (j < nl) {
           uu[r] = ldcg(&sl.nearq[j]);
           dd[r] = ldcg(&sl.d[uu[r]]);
           dn[r] = (D)__ldg(&a.g.dnode[uu[r]]);
-          out = dmin(out, (D)(dd[r] + dn[r]));
+          dni[r] = a.g.dnode_in ? (D)__ldg(&a.g.dnode_in[uu[r]]) : dn[r];
+          out = dmin(out, out_key<D>(dd[r], (uint32_t)dn[r]));
           dm = dmin(dm, dd[r]);
         }
       }
@@ -781,7 +814,7 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
         const uint32_t j = base + t;
         const uint32_t valid = j < nl;
         uint32_t take = valid && dd[r] < thr;
-        if (valid && a.settle_in && !take) take = dd[r] < (D)(dm + dn[r]);
+        if (valid && a.settle_in && !take) take = dd[r] < (D)(dm + dni[r]);
         uint32_t stot;
         const uint32_t sx = team_excl_scan<TEAM>(take, &stot, sh.scan);
         if (take) sl.S[S0 + nset + sx] = uu[r];
@@ -797,7 +830,7 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
         if (j < nl) {
           const uint32_t u = ldcg(&sl.nearq[j]);
           const D du = ldcg(&sl.d[u]);
-          out = dmin(out, (D)(du + (D)__ldg(&a.g.dnode[u])));
+          out = dmin(out, out_key<D>(du, __ldg(&a.g.dnode[u])));
           dm = dmin(dm, du);
         }
       }
@@ -811,7 +844,8 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
           u = ldcg(&sl.nearq[j]);
           const D du = ldcg(&sl.d[u]);
           take = du < thr;
-          if (a.settle_in && !take) take = du < (D)(dm + (D)__ldg(&a.g.dnode[u]));
+          if (a.settle_in && !take)
+            take = du < (D)(dm + (D)__ldg(a.g.dnode_in ? &a.g.dnode_in[u] : &a.g.dnode[u]));
         }
         uint32_t stot;
         const uint32_t sx = team_excl_scan<TEAM>(take, &stot, sh.scan);

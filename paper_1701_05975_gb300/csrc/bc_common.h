@@ -17,7 +17,13 @@ struct GraphDev {
   const uint2* adj;         // [nnz] {neighbour, weight}, or nullptr when adjp is used
   const uint32_t* adjp;     // [nnz] neighbour | weight << col_bits (graphs where both fit 32 bits)
   uint32_t col_bits;        // bits of the neighbour id in an adjp word
-  const uint32_t* dnode;    // [n] Delta_node(v) = min incident weight (UINT32_MAX if isolated)
+  const uint32_t* dnode;    // [n] Delta_node(v) = min incident (directed: outgoing) weight, UINT32_MAX if none
+  // Directed graphs only (nullptr otherwise): the in-edge CSR, same entry
+  // form as the out-edge one, and the minimum incoming weight per vertex.
+  const uint64_t* in_row_ptr;
+  const uint2* in_adj;
+  const uint32_t* in_adjp;
+  const uint32_t* dnode_in;
   // Optional relabeling (graph prep orders vertices by decreasing degree so
   // the state of high-degree vertices is contiguous).  Internal ids are
   // "new"; the caller's ids are "old".  All three are nullptr when the graph

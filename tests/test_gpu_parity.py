@@ -261,3 +261,38 @@ def test_wide_weights_use_unpacked_entries_and_64bit_distances():
             d, sg, _ = G.sssp_debug(0)
             d_ref, sg_ref, _ = oracle.sssp(g, 0)
             assert np.array_equal(d, d_ref) and np.array_equal(sg, sg_ref)
+
+
+@pytest.mark.parametrize("cfg", CONFIGS, ids=lambda c: f"team{c['team_threads']}-in{c['settle_in']}")
+def test_directed_small_graphs(cfg):
+    bc.bc_set_config(**cfg)
+    rng = np.random.default_rng(303)
+    for i in range(25):
+        n = int(rng.integers(1, 60))
+        g = gen.random_small_digraph(n, float(rng.choice([0.03, 0.1, 0.3])), 1, int(rng.choice([1, 4, 60])), rng)
+        src = np.arange(n, dtype=np.uint32)
+        with bc.Graph(g, flags=bc.BC_DIRECTED) as G:
+            assert G.info().directed == 1
+            assert_bc_close(G.compute(src, 1.0), oracle.bc_directed(g, src, 1.0))
+            ebc, _ = G.edge_compute(src, 1.0)
+            assert_bc_close(ebc, oracle.edge_bc(g, src, 1.0))
+            for s in (0, n - 1):
+                d, sg, lev = G.sssp_debug(s)
+                d_ref, sg_ref, _ = oracle.sssp(g, s)
+                assert np.array_equal(d, d_ref) and np.array_equal(sg, sg_ref)
+
+
+@pytest.mark.parametrize("layout", [bc.BC_RELABEL_DEGREE, bc.BC_KEEP_ORDER])
+def test_directed_rmat(layout):
+    g = gen.rmat_digraph(14, 8, wmin=1, wmax=255, seed=5)
+    src = gen.sample_sources(g.n, 64, seed=6)
+    want = oracle.bc_directed(g, src, 1.0)
+    with bc.Graph(g, flags=bc.BC_DIRECTED | layout) as G:
+        assert_bc_close(G.compute(src, 1.0), want)
+        d, sg, _ = G.sssp_debug(int(src[3]))
+        d_ref, sg_ref, _ = oracle.sssp(g, int(src[3]))
+        assert np.array_equal(d, d_ref) and np.array_equal(sg, sg_ref)
+        bc.bc_set_config(mode=bc.BC_MODE_PLAIN)
+        with pytest.raises(bc.BCError) as ei:
+            G.compute(src[:2], 1.0)
+        assert ei.value.code == bc.BC_ERR_INVALID
