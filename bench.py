@@ -34,6 +34,9 @@ WORKLOADS = {
     "serving": ("serving stream: Poisson arrivals over 15 graphs {ER avg deg 16, BA 4/vertex, perturbed grid} x "
                 "n in {1k, 4k, 16k, 65k, 262k}, weights U[1,1000]; exact BC for n <= 16k, else 256 sampled sources",
                 None),
+    "ablation": ("the paper's thread mappings (node-parallel / work-efficient x 1-32 threads per vertex) "
+                 "against the batched kernel on ER and Kronecker sweeps shaped like Fig. 4-5, weights U[1,10]",
+                 None),
     "rmat20": ("R-MAT scale 20, edge factor 16, a=.57 b=.19 c=.19, symmetrised, weights U[1,255], "
                "4096 uniform sources, scale 0.5 n/k", gen.workload_rmat20),
     "ba65k": ("Barabasi-Albert n=65536, 4 edges per new vertex, weights U[1,1000], all sources, scale 0.5",
@@ -208,6 +211,73 @@ def run_reference(args, g, sources, scale, desc):
     print(json.dumps(line), flush=True)
 
 
+def ablation_graphs():
+    """ER and Kronecker graphs shaped like the paper's Fig. 4(a-d) and Fig. 5(c, d)
+    (sizes, average degrees), weights uniform in [1, 10] as in its Sec. 4.1."""
+    out = []
+    for lg in (14, 16, 18):  # Fig. 4(a, b): average degree 32
+        out.append((f"ER n=2^{lg} deg 32", gen.er_graph(1 << lg, 16 << lg, 1, 10, seed=0)))
+        out.append((f"Kronecker 2^{lg} ef 16", gen.rmat_graph(lg, 16, wmin=1, wmax=10, seed=0)))
+    for deg in (4, 16, 64):  # Fig. 4(c, d): degree sweeps
+        out.append((f"ER n=20000 deg {deg}", gen.er_graph(20000, 10000 * deg, 1, 10, seed=0)))
+        out.append((f"Kronecker 2^15 ef {deg // 2}", gen.rmat_graph(15, deg // 2, wmin=1, wmax=10, seed=0)))
+    out.append(("ER n=2^17 deg 4", gen.er_graph(1 << 17, 2 << 17, 1, 10, seed=0)))  # Fig. 5(c)
+    out.append(("Kronecker 2^17 ef 2", gen.rmat_graph(17, 2, wmin=1, wmax=10, seed=0)))  # Fig. 5(d)
+    return out
+
+
+def run_ablation(args, desc):
+    """Per graph: each paper mapping and the batched kernel on the same sampled
+    sources; one JSON line per graph (seconds per source, phases per source =
+    the average search depth of Fig. 4(e))."""
+    import torch
+
+    import paper_1701_05975_gb300 as bc
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    k = args.sources or 4
+    rows = []
+    for name, g in ablation_graphs():
+        deg = g.degrees()
+        cand = np.flatnonzero(deg > 0)
+        src = np.sort(np.random.default_rng(0).choice(cand, size=min(k, len(cand)), replace=False)).astype(np.uint32)
+        res = {"graph": name, "n": g.n, "m": g.m, "sources": len(src)}
+        with bc.Graph(g) as G:
+            ref = None
+            for npar in (True, False):
+                for vw in (1, 4, 8, 16, 32):
+                    G.compute_paper_variant(src[:1], 1.0, node_parallel=npar, vwarp=vw)  # warm
+                    t0 = time.perf_counter()
+                    out = G.compute_paper_variant(src, 1.0, node_parallel=npar, vwarp=vw)
+                    dt = (time.perf_counter() - t0) / len(src)
+                    st = G.stats()
+                    res[f"{'np' if npar else 'we'}{vw}_ms_per_source"] = dt * 1e3
+                    res["depth_per_source"] = st.phases / max(st.sources, 1)
+                    if ref is None:
+                        ref = out.copy()
+                    assert np.allclose(out, ref, rtol=1e-9, atol=0)
+            G.compute(src[:1], 1.0)
+            t0 = time.perf_counter()
+            out = G.compute(src, 1.0)
+            res["batched_ms_per_source_few"] = (time.perf_counter() - t0) / len(src) * 1e3
+            assert np.allclose(out, ref, rtol=1e-9, atol=0)
+            many = np.arange(0, g.n, max(1, g.n // 2048), dtype=np.uint32)
+            t0 = time.perf_counter()
+            G.compute(many, 1.0)
+            res["batched_ms_per_source_2048"] = (time.perf_counter() - t0) / len(many) * 1e3
+        keys = [kk for kk in res if kk.endswith("_ms_per_source")]
+        res["best_paper_mapping"] = min(keys, key=lambda kk: res[kk]).replace("_ms_per_source", "")
+        rows.append(res)
+        if rank == 0:
+            print(json.dumps(res), flush=True)
+    if rank == 0:
+        we_better = sum(1 for r in rows if min(r[f"we{v}_ms_per_source"] for v in (1, 4, 8, 16, 32))
+                        <= min(r[f"np{v}_ms_per_source"] for v in (1, 4, 8, 16, 32)))
+        print(json.dumps({"metric": "ablation summary", "graphs": len(rows),
+                          "work_efficient_beats_node_parallel": we_better, "workload": desc}), flush=True)
+
+
 def run_serving_reference(args, desc):
     """The oracle over a bounded prefix of the same request stream."""
     ws, rank, _ = dist_env()
@@ -324,6 +394,9 @@ def main():
     args = ap.parse_args()
 
     desc, maker = WORKLOADS[args.workload]
+    if args.workload == "ablation":
+        run_ablation(args, desc)
+        return
     if args.workload == "serving":
         if args.impl == "reference":
             run_serving_reference(args, desc)

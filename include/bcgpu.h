@@ -168,6 +168,20 @@ int bc_edge_compute(bc_graph_t g, const uint32_t *sources, uint32_t k, double sc
                     double *out_bc);
 
 /*
+ * The paper's own thread mappings, for comparison (Sec. 3.1-3.4, Fig. 2-5):
+ * one source at a time over the whole GPU; each phase expands the frontier
+ * node-parallel (Algorithm 2: a group of vwarp threads per vertex of V,
+ * node_parallel = 1) or work-efficient (Algorithms 4-5: groups only for the
+ * frontier queue, node_parallel = 0) with vwarp in {1, 4, 8, 16, 32} threads
+ * per vertex (1 = thread per vertex, otherwise the warp-centric mapping of
+ * Sec. 3.4), then computes Delta_i (Eq. 2) and settles (Eq. 4) by scanning
+ * all V.  Same results as bc_compute (exact distances, FP64 sigma and BC);
+ * undirected graphs only.  sources[k] and out_bc[n] are HOST arrays.
+ */
+int bc_compute_paper_variant(bc_graph_t g, const uint32_t *sources, uint32_t k, double scale, double *out_bc,
+                             int node_parallel, int vwarp);
+
+/*
  * Serving (continuous batching).  Submit copies sources[k] at the call; the
  * HOST array out_bc[n] must stay valid until the request is DONE, FAILED or
  * CANCELLED.  Requests on different graphs and sizes are admitted as device

@@ -99,6 +99,7 @@ _SIGNATURES = {
     "bc_last_run_stats": [_vp, ctypes.POINTER(bc_run_stats)],
     "bc_autotune": [_vp, _vp, _u32],
     "bc_compute_noalloc": [_vp, _vp, _vp, _u32, _u64, _vp, _u32, _f64, _vp, _vp, _vp],
+    "bc_compute_paper_variant": [_vp, _vp, _u32, _f64, _vp, _int, _int],
 }
 
 _lib = None
@@ -181,6 +182,13 @@ def bc_compute(h, sources, scale: float, out_bc: np.ndarray):
 def bc_compute_async(h, d_sources_ptr: int, k: int, scale: float, d_out_ptr: int, stream_ptr: int):
     _check(lib().bc_compute_async(h, ctypes.c_void_p(d_sources_ptr), k, scale, ctypes.c_void_p(d_out_ptr),
                                   ctypes.c_void_p(stream_ptr)))
+
+
+def bc_compute_paper_variant(h, sources, scale: float, out_bc: np.ndarray, node_parallel: bool, vwarp: int):
+    src = np.ascontiguousarray(sources, dtype=np.uint32)
+    _check(lib().bc_compute_paper_variant(h, _ptr(src) if len(src) else None, len(src), scale, _ptr(out_bc),
+                                          int(node_parallel), vwarp))
+    return out_bc
 
 
 def bc_sync_status(h, stream_ptr: int):
@@ -273,6 +281,10 @@ class Graph:
         bc = np.empty(self.n, np.float64)
         bc_edge_compute(self.handle, sources, scale, ebc, bc)
         return ebc[: self.nnz], bc
+
+    def compute_paper_variant(self, sources, scale: float = 1.0, node_parallel: bool = False, vwarp: int = 32):
+        out = np.empty(self.n, np.float64)
+        return bc_compute_paper_variant(self.handle, sources, scale, out, node_parallel, vwarp)
 
     def sssp_debug(self, s: int):
         return bc_sssp_debug(self.handle, s, self.n)

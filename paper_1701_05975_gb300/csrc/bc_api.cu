@@ -165,6 +165,7 @@ struct bc_graph {
   bc_run_stats last{};
   std::atomic<int> serving_refs{0};
   PlainWork* plain = nullptr;
+  PaperWork* paper = nullptr;
   cudaStream_t stream = nullptr;  // internal stream of the synchronous calls
 };
 
@@ -809,6 +810,7 @@ int bc_graph_destroy(bc_graph_t g) {
   }
   g->pool.clear();
   plain_destroy(g->plain);
+  paper_destroy(g->paper);
   cudaFree(g->row_ptr);
   cudaFree(g->adj);
   cudaFree(g->adjp);
@@ -982,6 +984,42 @@ int bc_sssp_debug(bc_graph_t g, uint32_t s, uint64_t* out_dist, double* out_sigm
     if (out_level) out_level[ov] = level[v];
   }
   return BC_OK;
+}
+
+int bc_compute_paper_variant(bc_graph_t g, const uint32_t* sources, uint32_t k, double scale, double* out_bc,
+                             int node_parallel, int vwarp) {
+  if (int rc = check_graph(g)) return rc;
+  if (!out_bc || (k && !sources)) return fail(BC_ERR_INVALID, "null argument");
+  if (vwarp != 1 && vwarp != 4 && vwarp != 8 && vwarp != 16 && vwarp != 32)
+    return fail(BC_ERR_INVALID, "vwarp must be 1, 4, 8, 16 or 32");
+  if (g->directed) return fail(BC_ERR_INVALID, "the paper's mappings run undirected graphs only");
+  for (uint32_t i = 0; i < k; ++i)
+    if (sources[i] >= g->n) return fail(BC_ERR_INVALID, "source %u out of range (n = %u)", sources[i], g->n);
+  CK(cudaSetDevice(g->device));
+  RunCfg r = resolve(g);
+  cudaStream_t st = g->stream;
+  if (!g->paper) {
+    cudaError_t e;
+    g->paper = paper_create(g->n, g->dist_bits, &e);
+    if (!g->paper) return cuda_fail(e, "paper-variant workspace");
+  }
+  double* d_bc = nullptr;
+  CK(cudaMalloc(&d_bc, (size_t)g->n * 8));
+  cudaError_t e = cudaMemsetAsync(d_bc, 0, (size_t)g->n * 8, st);
+  int dev = DEV_OK;
+  unsigned long long stats[STAT_COUNT] = {0};
+  if (e == cudaSuccess)
+    e = paper_run(g->paper, view(g), g->dist_bits, sources, g->relabeled ? g->h_o2n.data() : nullptr, k, d_bc,
+                  node_parallel != 0, vwarp, r.phase_cap, g->sm_count, st, &dev, stats);
+  if (e == cudaSuccess && scale != 1.0) e = launch_scale(d_bc, g->n, scale, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out_bc, d_bc, (size_t)g->n * 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d_bc);
+  if (e != cudaSuccess) return cuda_fail(e, "paper-variant run");
+  Ctl c{};
+  memcpy(c.stats, stats, sizeof stats);
+  record_stats(g, c, r, 1);
+  return status_from_dev(dev);
 }
 
 int bc_last_run_stats(bc_graph_t g, bc_run_stats* out) {

@@ -122,6 +122,25 @@ cudaError_t launch_fill_slabs(char* base, uint64_t stride, uint32_t nslots, uint
 // Record a message for bc_last_error() on the calling thread; returns code.
 int set_error(int code, const char* msg);
 
+// The paper's thread mappings (bc_paper.cu): node-parallel or work-efficient
+// expansion with VW threads per vertex, Delta_i and settle over all V.
+struct PaperWork {
+  uint32_t n = 0;
+  void* d = nullptr;
+  double* sig = nullptr;
+  uint32_t* S = nullptr;
+  uint8_t* U = nullptr;
+  uint8_t* F = nullptr;
+  void* ctr = nullptr;
+  void* host_ctr = nullptr;  // pinned
+};
+PaperWork* paper_create(uint32_t n, int dist_bits, cudaError_t* e);
+void paper_destroy(PaperWork* w);
+uint64_t paper_bytes(uint32_t n, int dist_bits);
+cudaError_t paper_run(PaperWork* w, const GraphDev& g, int dist_bits, const uint32_t* host_sources,
+                      const uint32_t* host_o2n, uint32_t k, double* bc, bool node_parallel, int vwarp,
+                      uint64_t phase_cap, int sm_count, cudaStream_t st, int* status, unsigned long long* stats);
+
 }  // namespace bcgpu
 
 struct bc_graph;

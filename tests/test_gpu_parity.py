@@ -296,3 +296,24 @@ def test_directed_rmat(layout):
         with pytest.raises(bc.BCError) as ei:
             G.compute(src[:2], 1.0)
         assert ei.value.code == bc.BC_ERR_INVALID
+
+
+@pytest.mark.parametrize("node_parallel", [True, False])
+@pytest.mark.parametrize("vwarp", [1, 4, 8, 16, 32])
+def test_paper_thread_mappings_match_oracle(node_parallel, vwarp):
+    rng = np.random.default_rng(vwarp + 100 * node_parallel)
+    graphs = [gen.random_small_graph(int(rng.integers(1, 50)), 0.2, 1, 10, rng) for _ in range(6)]
+    graphs += [gen.er_graph(700, 5000, 1, 10, seed=8), gen.rmat_graph(10, 8, wmin=1, wmax=10, seed=9)]
+    # a graph with unreached vertices and 32-bit distances
+    graphs.append(gen.er_graph(3000, 1500, 1, 10, seed=10))
+    for g in graphs:
+        src = np.arange(0, g.n, max(1, g.n // 40), dtype=np.uint32)
+        with bc.Graph(g) as G:
+            got = G.compute_paper_variant(src, 0.5, node_parallel=node_parallel, vwarp=vwarp)
+            assert_bc_close(got, oracle.bc(g, src, 0.5))
+            assert G.stats().sources == len(src)
+            # the replay of Algorithm 2 settles exactly the oracle replay's batches
+            for s in src[:3]:
+                G.compute_paper_variant(np.array([s], np.uint32), 1.0, node_parallel=node_parallel, vwarp=vwarp)
+                nlev = oracle.phased(g, int(s))[4]
+                assert G.stats().phases == nlev - 1
