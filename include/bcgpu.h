@@ -66,6 +66,15 @@ extern "C" {
 #define BC_MODE_BATCHED 0u /* persistent launch: one team (warp or CTA) per source, many sources in flight */
 #define BC_MODE_PLAIN 1u   /* one source at a time over the whole GPU, host-driven phase loop */
 
+/* ---- per-source schedules of the batched mode --------------------------- */
+#define BC_ALGO_AUTO 0u   /* the graph's tuned schedule, else BC_ALGO_STRICT */
+#define BC_ALGO_STRICT 1u /* the paper's phases: settle every vertex that meets the strict OUT (Eq. 2 + Eq. 4) or
+                             IN criterion, sigma pulled as each batch settles (Sec. 3.2, Algorithm 2) */
+#define BC_ALGO_DELTA 2u  /* distances by delta-stepping rounds (bucket width = bucket_width), then predecessor
+                             counts, sigma pushed down the shortest-path DAG in hop-depth levels, and the
+                             dependency pull of Algorithm 3 over those levels in reverse.  Same results; far
+                             fewer synchronised steps on high-diameter graphs. */
+
 /* ---- request states (bc_request_poll) ---------------------------------- */
 #define BC_REQ_QUEUED 0
 #define BC_REQ_RUNNING 1
@@ -91,6 +100,7 @@ typedef struct bc_config {
   double mem_fraction;    /* share of free device memory the slabs may take (0 < f <= 0.95) */
   uint32_t warp_degree;   /* forward expansion: rows with at least this many entries get one warp each */
   uint32_t team_degree;   /* ... and rows with at least this many entries the whole team (>= warp_degree) */
+  uint32_t algorithm;     /* BC_ALGO_AUTO, BC_ALGO_STRICT or BC_ALGO_DELTA (batched mode) */
 } bc_config;
 
 /* Read the current process-wide configuration. */
@@ -253,12 +263,14 @@ typedef struct bc_run_stats {
   uint64_t cycles_backward; /* dependency accumulation */
   uint64_t near_scanned;    /* near-queue entries read by threshold and settle */
   uint64_t far_scanned;     /* far-queue entries read by refills */
+  uint64_t levels;          /* backward levels summed over sources (settle batches, or DAG hop depths) */
+  uint32_t algorithm;       /* schedule of the run: BC_ALGO_STRICT or BC_ALGO_DELTA */
 } bc_run_stats;
 
 int bc_last_run_stats(bc_graph_t g, bc_run_stats *out);
 
 /*
- * Autotuner: times candidate (team size, bucket width, settle rule) settings
+ * Autotuner: times candidate (schedule, team size, bucket width) settings
  * on a probe sample of `sources` (k_probe of them, HOST array) and stores the
  * fastest as the graph's tuned configuration, used whenever the process-wide
  * config leaves a field at 0.  Results are cached per graph fingerprint.

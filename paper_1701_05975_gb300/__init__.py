@@ -32,6 +32,7 @@ BC_KEEP_ORDER = 4
 BC_DIRECTED = 8
 BC_MODE_BATCHED = 0
 BC_MODE_PLAIN = 1
+BC_ALGO_AUTO, BC_ALGO_STRICT, BC_ALGO_DELTA = 0, 1, 2
 BC_REQ_QUEUED, BC_REQ_RUNNING, BC_REQ_DONE, BC_REQ_FAILED, BC_REQ_CANCELLED = range(5)
 
 _ERR_NAMES = {1: "BC_ERR_INVALID", 2: "BC_ERR_NOMEM", 3: "BC_ERR_CUDA", 4: "BC_ERR_TIMEOUT", 5: "BC_ERR_BUSY",
@@ -47,7 +48,8 @@ class BCError(RuntimeError):
 class bc_config(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_uint32), ("team_threads", ctypes.c_uint32), ("max_slots", ctypes.c_uint32),
                 ("settle_in", ctypes.c_uint32), ("bucket_width", ctypes.c_uint64), ("phase_cap", ctypes.c_uint64),
-                ("mem_fraction", ctypes.c_double), ("warp_degree", ctypes.c_uint32), ("team_degree", ctypes.c_uint32)]
+                ("mem_fraction", ctypes.c_double), ("warp_degree", ctypes.c_uint32), ("team_degree", ctypes.c_uint32),
+                ("algorithm", ctypes.c_uint32)]
 
 
 class bc_graph_info(ctypes.Structure):
@@ -64,7 +66,7 @@ class bc_run_stats(ctypes.Structure):
                 ("pair_overflows", ctypes.c_uint64), ("cycles_expand", ctypes.c_uint64),
                 ("cycles_refill", ctypes.c_uint64), ("cycles_settle", ctypes.c_uint64),
                 ("cycles_backward", ctypes.c_uint64), ("near_scanned", ctypes.c_uint64),
-                ("far_scanned", ctypes.c_uint64)]
+                ("far_scanned", ctypes.c_uint64), ("levels", ctypes.c_uint64), ("algorithm", ctypes.c_uint32)]
 
 
 class bc_serving_stats(ctypes.Structure):

@@ -90,6 +90,8 @@ SlabLayout make_layout(uint32_t n, int dist_bits) {
   L.pair_cap = (uint32_t)std::min<uint64_t>(2ull * n + 64, 0xffffffffull);
   L.off_pairs = off;
   off += align256((uint64_t)L.pair_cap * 8);
+  L.off_pc = off;
+  off += align256((uint64_t)n * 4);
   L.stride = off;
   return L;
 }
@@ -126,6 +128,7 @@ struct TuneCfg {
   uint32_t max_slots = 0;  // 0: the full resident capacity
   uint32_t warp_deg = 0;
   uint32_t team_deg = 0;
+  uint32_t algo = 0;
 };
 
 std::mutex g_tune_mu;
@@ -214,6 +217,7 @@ struct RunCfg {
   uint32_t mode;
   uint32_t warp_deg;
   uint32_t team_deg;
+  uint32_t algo;  // ALGO_STRICT or ALGO_DELTA
 };
 
 RunCfg resolve(const bc_graph* g) {
@@ -235,13 +239,15 @@ RunCfg resolve(const bc_graph* g) {
   r.warp_deg = c.warp_degree ? c.warp_degree : (g->tuned.warp_deg ? g->tuned.warp_deg : 32u);
   r.team_deg = c.team_degree ? c.team_degree : (g->tuned.team_deg ? g->tuned.team_deg : 8u * r.team);
   r.team_deg = std::max(r.team_deg, r.warp_deg);
+  const uint32_t al = c.algorithm ? c.algorithm : (g->tuned.algo ? g->tuned.algo : (uint32_t)BC_ALGO_STRICT);
+  r.algo = (al == BC_ALGO_DELTA) ? ALGO_DELTA : ALGO_STRICT;
   return r;
 }
 
 // Number of sources in flight for a run of k sources.
 int plan_slots(const bc_graph* g, const RunCfg& r, uint32_t k, uint32_t* slots_out) {
   int bps = 0;
-  cudaError_t e = batched_occupancy(g->dist_bits, (int)r.team, &bps);
+  cudaError_t e = batched_occupancy(g->dist_bits, (int)r.team, (int)r.algo, &bps);
   if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
   const uint32_t per_block = (uint32_t)(batched_block_threads((int)r.team) / (int)r.team);
   uint64_t slots = (uint64_t)std::max(bps, 1) * g->sm_count * per_block;
@@ -285,6 +291,8 @@ int ws_acquire(bc_graph* g, uint32_t slots, uint32_t k, cudaStream_t st, Workspa
                             align256((uint64_t)g->n * (g->dist_bits / 8)), 0xffffffffu, st);
     if (e == cudaSuccess)
       e = launch_fill_slabs(nw->slabs, nw->lay.stride, slots, nw->lay.off_acc, align256((uint64_t)g->n * 8), 0u, st);
+    if (e == cudaSuccess)
+      e = launch_fill_slabs(nw->slabs, nw->lay.stride, slots, nw->lay.off_pc, align256((uint64_t)g->n * 4), 0u, st);
     if (e != cudaSuccess) {
       ws_free(nw.get());
       return cuda_fail(e, "workspace allocation");
@@ -342,6 +350,7 @@ BatchArgs make_args(bc_graph* g, Workspace* w, const RunCfg& r, const uint32_t* 
   a.debug_out = w->ctl->debug;
   a.warp_deg = r.warp_deg;
   a.team_deg = r.team_deg;
+  a.algo = r.algo;
   // the highest-degree vertices after relabeling: 128 KiB of 32-bit distance
   // words per source (the whole L2 holds this prefix for ~1000 sources)
   a.hot_n = g->relabeled ? std::min<uint32_t>(g->n, 32768u) : 0u;
@@ -371,6 +380,7 @@ int status_from_dev(int dev) {
   if (dev == DEV_OK) return BC_OK;
   if (dev == DEV_ERR_TIMEOUT) return fail(BC_ERR_TIMEOUT, "device phase cap reached (BC_ERR_TIMEOUT)");
   if (dev == DEV_ERR_INVALID) return fail(BC_ERR_INVALID, "a source is out of range");
+  if (dev == DEV_ERR_INTERNAL) return fail(BC_ERR_CUDA, "device consistency check failed (DAG levels do not cover the reached set)");
   return fail(BC_ERR_CUDA, "unknown device status %d", dev);
 }
 
@@ -390,6 +400,8 @@ void record_stats(bc_graph* g, const Ctl& c, const RunCfg& r, uint32_t slots) {
   g->last.cycles_backward = c.stats[STAT_CYC_BACKWARD];
   g->last.near_scanned = c.stats[STAT_NEAR_SCANNED];
   g->last.far_scanned = c.stats[STAT_FAR_SCANNED];
+  g->last.levels = c.stats[STAT_LEVELS];
+  g->last.algorithm = r.algo == ALGO_DELTA ? BC_ALGO_DELTA : BC_ALGO_STRICT;
   g->last.team_threads = r.team;
   g->last.slots = slots;
   g->last.bucket_width = r.width;
@@ -517,7 +529,7 @@ void bcgpu::graph_serving_ref(bc_graph* g, int delta) { g->serving_refs += delta
 int bcgpu::serve_plan(bc_graph* g, ServePlan* out) {
   RunCfg r = resolve(g);
   int bps = 0;
-  cudaError_t e = batched_occupancy(g->dist_bits, (int)r.team, &bps);
+  cudaError_t e = batched_occupancy(g->dist_bits, (int)r.team, (int)r.algo, &bps);
   if (e != cudaSuccess) return cuda_fail(e, "occupancy");
   const uint32_t per_block = (uint32_t)(batched_block_threads((int)r.team) / (int)r.team);
   out->team = r.team;
@@ -598,6 +610,7 @@ int bc_set_config(const bc_config* cfg) {
       cfg->team_threads != 512)
     return fail(BC_ERR_INVALID, "team_threads must be 0, 32, 128, 256 or 512");
   if (cfg->settle_in > 2) return fail(BC_ERR_INVALID, "settle_in must be 0, 1 or 2");
+  if (cfg->algorithm > BC_ALGO_DELTA) return fail(BC_ERR_INVALID, "algorithm must be 0, 1 or 2");
   if (cfg->mem_fraction < 0 || cfg->mem_fraction > 0.95) return fail(BC_ERR_INVALID, "mem_fraction out of range");
   if (cfg->team_degree && cfg->warp_degree && cfg->team_degree < cfg->warp_degree)
     return fail(BC_ERR_INVALID, "team_degree must be >= warp_degree");
@@ -874,6 +887,7 @@ int bc_compute_async(bc_graph_t g, const uint32_t* d_sources, uint32_t k, double
   {
     std::lock_guard<std::mutex> lk(g->mu);
     g->async_ws[st] = w;
+    g->last.algorithm = r.algo == ALGO_DELTA ? BC_ALGO_DELTA : BC_ALGO_STRICT;
     g->last.team_threads = r.team;
     g->last.slots = slots;
     g->last.bucket_width = r.width;
@@ -911,6 +925,7 @@ int bc_sync_status(bc_graph_t g, void* stream) {
     g->last.cycles_backward = c.stats[STAT_CYC_BACKWARD];
     g->last.near_scanned = c.stats[STAT_NEAR_SCANNED];
     g->last.far_scanned = c.stats[STAT_FAR_SCANNED];
+    g->last.levels = c.stats[STAT_LEVELS];
   }
   return status_from_dev(w->host_ctl->err);
 }
@@ -1052,12 +1067,15 @@ int bc_autotune(bc_graph_t g, const uint32_t* sources, uint32_t k_probe) {
   RunCfg base = resolve(g);
   base.mode = BC_MODE_BATCHED;
   base.settle_in = 1;
+  base.algo = (user.algorithm == BC_ALGO_DELTA) ? ALGO_DELTA : ALGO_STRICT;
   double ms = 0;
   if (int rc = timed(base, &ms)) return rc;  // warm-up: workspace allocation
   double best_ms = 1e300;
+  double best_phases = 0;  // settle phases per source of the fastest strict candidate
   TuneCfg best;
   for (uint32_t team : teams) {
     if (user.team_threads && user.team_threads != team) continue;
+    if (user.algorithm == BC_ALGO_DELTA) break;
     for (uint64_t width : widths) {
       if (user.bucket_width && user.bucket_width != width) continue;
       RunCfg r = base;
@@ -1069,6 +1087,35 @@ int bc_autotune(bc_graph_t g, const uint32_t* sources, uint32_t k_probe) {
         best.team = team;
         best.width = width;
         best.settle_in = 1;
+        best.algo = BC_ALGO_STRICT;
+        std::lock_guard<std::mutex> lk(g->mu);
+        best_phases = g->last.sources ? (double)g->last.phases / (double)g->last.sources : 0.0;
+      }
+    }
+  }
+  // the delta-stepping schedule, buckets one to sixteen maximum weights wide:
+  // it walks every reached row about four times (rounds, predecessor count,
+  // sigma push, backward) against about once, so it is only a candidate where
+  // the strict schedule needs many settle phases per source (high diameter)
+  if (user.algorithm == BC_ALGO_DELTA || (user.algorithm == BC_ALGO_AUTO && best_phases >= 1000.0)) {
+    for (uint32_t team : teams) {
+      if (user.team_threads && user.team_threads != team) continue;
+      if (!user.team_threads && best.team && team != best.team) continue;
+      for (uint64_t m : {1ull, 4ull, 16ull}) {
+        const uint64_t width = std::max<uint64_t>(1, g->max_w) * m;
+        if (user.bucket_width && user.bucket_width != width) continue;
+        RunCfg r = base;
+        r.algo = ALGO_DELTA;
+        r.team = team;
+        r.width = width;
+        if (int rc = timed(r, &ms)) return rc;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best.team = team;
+          best.width = width;
+          best.settle_in = 1;
+          best.algo = BC_ALGO_DELTA;
+        }
       }
     }
   }
@@ -1078,6 +1125,7 @@ int bc_autotune(bc_graph_t g, const uint32_t* sources, uint32_t k_probe) {
     RunCfg r = base;
     r.team = best.team;
     r.width = best.width;
+    r.algo = best.algo == BC_ALGO_DELTA ? ALGO_DELTA : ALGO_STRICT;
     uint32_t full = 0;
     if (int rc = plan_slots(g, r, k_probe, &full)) return rc;
     r.max_slots = std::max<uint32_t>(1, full / 2);

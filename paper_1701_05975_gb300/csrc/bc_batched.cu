@@ -115,6 +115,10 @@ struct TeamShared {
   uint32_t wlist[TEAM];  // chunk vertices walked by one warp each
   uint32_t tlist[TEAM];  // chunk vertices walked by the whole team
   uint32_t wnext, nwl, ntl;
+  // delta-stepping schedule
+  uint32_t front_len, def_len, lvl_len, round;
+  uint32_t* front_out;
+  D bound;
   D red[2 * (TEAM / 32) + 2];
   uint32_t scan[2 * (TEAM / 32 + 1)];
 };
@@ -333,6 +337,7 @@ struct Slab {
   uint32_t* pend;   // pend[l] = end of level l's DAG edges in pairs
   uint2* pairs;     // DAG edges {predecessor u, vertex v}
   uint32_t pair_cap;
+  uint32_t* pc;     // delta-stepping: round stamps, then predecessor counts (zero between sources)
 };
 
 template <typename D>
@@ -350,6 +355,7 @@ __device__ __forceinline__ Slab<D> slab_at(const BatchArgs& a, uint32_t slot) {
   s.pend = reinterpret_cast<uint32_t*>(base + a.lay.off_pend);
   s.pairs = reinterpret_cast<uint2*>(base + a.lay.off_pairs);
   s.pair_cap = a.lay.pair_cap;
+  s.pc = reinterpret_cast<uint32_t*>(base + a.lay.off_pc);
   return s;
 }
 
@@ -357,10 +363,11 @@ __device__ __forceinline__ Slab<D> slab_at(const BatchArgs& a, uint32_t slot) {
 // the degrees.  Returns the chunk's edge total (uniform over the team).
 template <typename D, int TEAM>
 __device__ __forceinline__ uint32_t load_chunk(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, TEAM>& sh,
-                                               uint32_t base, uint32_t cnt, int t, bool want_sigma) {
+                                               const uint32_t* list, uint32_t base, uint32_t cnt, int t,
+                                               bool want_sigma) {
   uint32_t deg = 0;
   if ((uint32_t)t < cnt) {
-    uint32_t v = ldcg(&sl.S[base + t]);
+    uint32_t v = ldcg(&list[base + t]);
     uint64_t r0 = __ldg(&a.g.row_ptr[v]);
     uint64_t r1 = __ldg(&a.g.row_ptr[v + 1]);
     deg = (uint32_t)(r1 - r0);
@@ -395,7 +402,11 @@ __device__ __forceinline__ uint32_t owner_of(const uint32_t* off, uint32_t cnt, 
 // Walk modes: an undirected row serves both the sigma pull and the
 // relaxation; a directed graph pulls over its in-edges and relaxes over its
 // out-edges in two walks.
-enum : int { WALK_BOTH = 0, WALK_PULL = 1, WALK_RELAX = 2 };
+// The delta-stepping schedule adds three walks: relaxation into the next
+// round's frontier (WALK_DS), counting each vertex's predecessors once the
+// distances are final (WALK_COUNT), and pushing sigma down the DAG level by
+// level (WALK_KAHN).
+enum : int { WALK_BOTH = 0, WALK_PULL = 1, WALK_RELAX = 2, WALK_DS = 3, WALK_COUNT = 4, WALK_KAHN = 5 };
 
 template <typename D, int TEAM, int MODE>
 __device__ __forceinline__ void visit_entry(const Slab<D>& sl, TeamShared<D, TEAM>& sh, uint32_t i, uint2 ent, D du,
@@ -404,6 +415,33 @@ __device__ __forceinline__ void visit_entry(const Slab<D>& sl, TeamShared<D, TEA
   const uint32_t u = ent.x;
   const D w = (D)ent.y;
   const D dvi = sh.dv[i];
+  if constexpr (MODE == WALK_DS) {
+    const D nd = dvi + w;
+    if (nd < du) {
+      ++relax;
+      const D old = atomic_min_d(&sl.d[u], nd);
+      if (nd < old) {
+        if (old == INF) sl.S[atomicAdd(&sh.S_len, 1u)] = u;  // reached list
+        if (nd < sh.bound) {
+          // once per round in the next frontier (stamp = that round)
+          if (atomicExch(&sl.pc[u], sh.round) != sh.round) sh.front_out[atomicAdd(&sh.front_len, 1u)] = u;
+        } else if (old == INF) {
+          sl.farq2[atomicAdd(&sh.def_len, 1u)] = u;  // deferred to a later bucket
+        }
+      }
+    }
+    return;
+  } else if constexpr (MODE == WALK_COUNT) {
+    if (du != INF && du + w == dvi) atomicAdd(&sh.acc[i], 1.0);
+    return;
+  } else if constexpr (MODE == WALK_KAHN) {
+    if (du != INF && du == dvi + w) {
+      // u is a successor: push sigma; the last predecessor releases u
+      atomicAdd(&sl.sig[u], sh.sv[i]);
+      if (atomicSub(&sl.pc[u], 1u) == 1u) sl.ends[atomicAdd(&sh.lvl_len, 1u)] = u;
+    }
+    return;
+  }
   if (MODE != WALK_RELAX && du != INF && du + w == dvi) {
     atomicAdd(&sh.acc[i], ldg_slab(&sl.sig[u]));
     const uint32_t pos = atomicAdd(&sh.pair_len, 1u);
@@ -467,8 +505,8 @@ __device__ __forceinline__ void walk_row(const BatchArgs& a, const Rows& rows, c
 // tiers, so threads that finish one move on to the next.
 template <typename D, int TEAM, bool PACKED, int MODE>
 __device__ void expand_forward(const BatchArgs& a, const Rows& rows, const Slab<D>& sl, TeamShared<D, TEAM>& sh,
-                               uint32_t f0, uint32_t f1, uint32_t s, int t, D split, unsigned long long& relax,
-                               unsigned long long& scanned) {
+                               const uint32_t* list, uint32_t f0, uint32_t f1, uint32_t s, int t, D split,
+                               unsigned long long& relax, unsigned long long& scanned) {
   const D INF = dinf<D>();
   const uint32_t warp_deg = a.warp_deg;
   const uint32_t team_deg = (TEAM == 32) ? a.warp_deg : a.team_deg;
@@ -476,7 +514,7 @@ __device__ void expand_forward(const BatchArgs& a, const Rows& rows, const Slab<
     const uint32_t cnt = min((uint32_t)TEAM, f1 - base);
     uint32_t deg = 0, small = 0, is_w = 0, is_t = 0;
     if ((uint32_t)t < cnt) {
-      const uint32_t v = ldcg(&sl.S[base + t]);
+      const uint32_t v = ldcg(&list[base + t]);
       const uint64_t r0 = __ldg(&rows.row_ptr[v]);
       deg = (uint32_t)(__ldg(&rows.row_ptr[v + 1]) - r0);
       sh.vtx[t] = v;
@@ -484,6 +522,7 @@ __device__ void expand_forward(const BatchArgs& a, const Rows& rows, const Slab<
       sh.dg[t] = deg;
       sh.dv[t] = ldcg(&sl.d[v]);
       sh.acc[t] = 0.0;
+      if (MODE == WALK_KAHN) sh.sv[t] = ldcg(&sl.sig[v]);
       if (deg >= team_deg) is_t = 1;
       else if (deg >= warp_deg) is_w = 1;
       else small = deg;
@@ -545,20 +584,27 @@ __device__ void expand_forward(const BatchArgs& a, const Rows& rows, const Slab<
         if (iv[q] != NONE) visit_entry<D, TEAM, MODE>(sl, sh, iv[q], ent[q], dus[q], split, relax);
     }
     team_sync<TEAM>();
-    if (MODE != WALK_RELAX && (uint32_t)t < cnt && sh.vtx[t] != s) sl.sig[sh.vtx[t]] = sh.acc[t];
+    if ((MODE == WALK_BOTH || MODE == WALK_PULL) && (uint32_t)t < cnt && sh.vtx[t] != s)
+      sl.sig[sh.vtx[t]] = sh.acc[t];
+    if (MODE == WALK_COUNT && (uint32_t)t < cnt) {
+      const uint32_t v = sh.vtx[t];
+      sl.pc[v] = (uint32_t)sh.acc[t];
+      sl.sig[v] = (v == s) ? 1.0 : 0.0;
+    }
     team_sync<TEAM>();
   }
 }
 
 // Backward (Algorithm 3) over one level S[f0, f1).
 template <typename D, int TEAM, bool PACKED>
-__device__ void accumulate_level(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, TEAM>& sh, uint32_t f0,
-                                 uint32_t f1, uint32_t s, int t, unsigned long long& scanned) {
+__device__ void accumulate_level(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, TEAM>& sh,
+                                 const uint32_t* list, uint32_t f0, uint32_t f1, uint32_t s, int t,
+                                 unsigned long long& scanned) {
   const D INF = dinf<D>();
   const bool edges = a.ebc != nullptr;
   for (uint32_t base = f0; base < f1; base += TEAM) {
     const uint32_t cnt = min((uint32_t)TEAM, f1 - base);
-    const uint32_t total = load_chunk<D, TEAM>(a, sl, sh, base, cnt, t, edges);
+    const uint32_t total = load_chunk<D, TEAM>(a, sl, sh, list, base, cnt, t, edges);
     scanned += (t == 0) ? total : 0;
     for (uint32_t e0 = t; e0 < total; e0 += TEAM * UNROLL) {
       uint32_t iv[UNROLL];
@@ -675,10 +721,13 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
     c0 = clock64();
     if (a.g.in_row_ptr) {
       // directed: sigma from in-edges, then relax out-edges
-      expand_forward<D, TEAM, PACKED, WALK_PULL>(a, in_rows(a.g), sl, sh, f0, f1, s, t, split0, relax, scanned);
-      expand_forward<D, TEAM, PACKED, WALK_RELAX>(a, out_rows(a.g), sl, sh, f0, f1, s, t, split0, relax, scanned);
+      expand_forward<D, TEAM, PACKED, WALK_PULL>(a, in_rows(a.g), sl, sh, sl.S, f0, f1, s, t, split0, relax,
+                                                  scanned);
+      expand_forward<D, TEAM, PACKED, WALK_RELAX>(a, out_rows(a.g), sl, sh, sl.S, f0, f1, s, t, split0, relax,
+                                                   scanned);
     } else {
-      expand_forward<D, TEAM, PACKED, WALK_BOTH>(a, out_rows(a.g), sl, sh, f0, f1, s, t, split0, relax, scanned);
+      expand_forward<D, TEAM, PACKED, WALK_BOTH>(a, out_rows(a.g), sl, sh, sl.S, f0, f1, s, t, split0, relax,
+                                                  scanned);
     }
     // DAG edges into the batch just expanded end here
     if (t == 0) sl.pend[sh.nlev - 1] = sh.pair_len;
@@ -906,7 +955,7 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
       for (int lev = (int)nlev - 1; lev >= last; --lev) {
         const uint32_t b0 = ldcg(&sl.ends[lev]);
         const uint32_t b1 = ldcg(&sl.ends[lev + 1]);
-        accumulate_level<D, TEAM, PACKED>(a, sl, sh, b0, b1, s, t, scanned);
+        accumulate_level<D, TEAM, PACKED>(a, sl, sh, sl.S, b0, b1, s, t, scanned);
       }
     }
     cyc_back += clock64() - c0;
@@ -931,6 +980,7 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
       atomicAdd(&a.stats[STAT_REFILLS], (unsigned long long)refills);
       atomicAdd(&a.stats[STAT_REACHED], (unsigned long long)sh.S_len);
       atomicAdd(&a.stats[STAT_DAG_EDGES], (unsigned long long)sh.pair_len);
+      atomicAdd(&a.stats[STAT_LEVELS], (unsigned long long)sh.nlev);
       atomicAdd(&a.stats[STAT_PAIR_OVERFLOW], (unsigned long long)sh.pair_over);
       atomicAdd(&a.stats[STAT_CYC_EXPAND], cyc_expand);
       atomicAdd(&a.stats[STAT_CYC_REFILL], cyc_refill);
@@ -945,7 +995,204 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
 }
 
 
-template <typename D, int TEAM, int BLOCK, bool PACKED>
+// Delta-stepping schedule (ALGO_DELTA), for graphs whose strict settle batches
+// are many and small (high diameter):
+//   1. exact distances by delta-stepping rounds: the frontier relaxes its
+//      out-edges; improved vertices below the bucket bound form the next
+//      round's frontier (each at most once per round), the rest wait in a
+//      deferred list until the bound advances;
+//   2. one walk counts each reached vertex's shortest-path predecessors;
+//   3. sigma is pushed down the shortest-path DAG level by level (Kahn's
+//      order): a vertex joins the next level when its last predecessor has
+//      pushed to it, so a level holds vertices of equal DAG hop depth and no
+//      DAG edge lies inside a level (FP64 atomic sums of integer counts are
+//      exact below 2^53);
+//   4. Algorithm 3 over those levels in reverse (pull from successors).
+// Returns false on a cap hit or a failed consistency check (slab restored).
+template <typename D, int TEAM, bool PACKED>
+__device__ bool run_source_ds(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, TEAM>& sh, uint32_t s, int t) {
+  const D INF = dinf<D>();
+  unsigned long long relax = 0, scanned = 0;
+  uint64_t rounds = 0, advances = 0;
+  unsigned long long cyc_expand = 0, cyc_refill = 0, cyc_settle = 0, cyc_back = 0, far_sc = 0;
+  long long c0 = clock64();
+  uint32_t* qa = sl.nearq;  // current frontier (stamp = sh.round)
+  uint32_t* qb = sl.farq;   // next frontier
+  if (t == 0) {
+    sl.d[s] = 0;
+    sl.S[0] = s;
+    sh.S_len = 1;
+    qa[0] = s;
+    sl.pc[s] = 1;
+    sh.round = 1;
+    sh.def_len = 0;
+    sh.bound = sat_add<D>((D)0, a.width);
+    sh.stop = 0;
+  }
+  team_sync<TEAM>();
+  uint32_t alen = 1;
+  int err = DEV_OK;
+  for (;;) {
+    c0 = clock64();
+    team_sync<TEAM>();  // every thread has read the last frontier length
+    if (t == 0) {
+      sh.front_out = qb;
+      sh.front_len = 0;
+      sh.round += 1;
+    }
+    team_sync<TEAM>();
+    expand_forward<D, TEAM, PACKED, WALK_DS>(a, out_rows(a.g), sl, sh, qa, 0, alen, s, t, INF, relax, scanned);
+    cyc_expand += clock64() - c0;
+    ++rounds;
+    alen = sh.front_len;
+    uint32_t* tmp = qa;
+    qa = qb;
+    qb = tmp;
+    if (alen == 0) {
+      c0 = clock64();
+      // next bucket: the deferred vertices within one width of the smallest
+      while (alen == 0 && sh.def_len > 0) {
+        const D old = sh.bound;
+        const uint32_t dl = sh.def_len;
+        far_sc += 2ull * dl;
+        D lo = INF, dummy = INF;
+        for (uint32_t base = 0; base < dl; base += TEAM) {
+          const uint32_t j = base + t;
+          if (j < dl) {
+            const D du = ldcg(&sl.d[ldcg(&sl.farq2[j])]);
+            if (du >= old) lo = dmin(lo, du);
+          }
+        }
+        team_min2<D, TEAM>(lo, dummy, sh.red);
+        const D nb = (lo == INF) ? old : sat_add<D>(lo, a.width);
+        if (t == 0) sh.front_len = 0;
+        team_sync<TEAM>();
+        uint32_t kept = 0;
+        for (uint32_t base = 0; base < dl; base += TEAM) {
+          const uint32_t j = base + t;
+          uint32_t u = 0, keep = 0;
+          if (j < dl) {
+            u = ldcg(&sl.farq2[j]);
+            const D du = ldcg(&sl.d[u]);
+            if (du >= old) {  // below old: already relaxed in an earlier bucket
+              if (du < nb) {
+                if (atomicExch(&sl.pc[u], sh.round) != sh.round) qa[atomicAdd(&sh.front_len, 1u)] = u;
+              } else {
+                keep = 1;
+              }
+            }
+          }
+          uint32_t ktot;
+          const uint32_t kx = team_excl_scan<TEAM>(keep, &ktot, sh.scan);
+          if (TEAM == 32) __syncwarp();
+          if (keep) sl.farq2[kept + kx] = u;
+          kept += ktot;
+        }
+        team_sync<TEAM>();
+        if (t == 0) {
+          sh.def_len = kept;
+          sh.bound = nb;
+        }
+        ++advances;
+        team_sync<TEAM>();
+        alen = sh.front_len;
+      }
+      cyc_refill += clock64() - c0;
+      if (alen == 0) break;
+    }
+    if (rounds + advances > a.phase_cap) {
+      err = DEV_ERR_TIMEOUT;
+      break;
+    }
+  }
+  uint32_t nlev = 0;
+  const uint32_t nr = sh.S_len;
+  if (err == DEV_OK) {
+    // distances are final: count predecessors (in-edges for directed graphs)
+    c0 = clock64();
+    const Rows prow = a.g.in_row_ptr ? in_rows(a.g) : out_rows(a.g);
+    expand_forward<D, TEAM, PACKED, WALK_COUNT>(a, prow, sl, sh, sl.S, 0, nr, s, t, INF, relax, scanned);
+    // sigma down the DAG, one hop-depth level at a time
+    if (t == 0) {
+      sl.ends[0] = s;
+      sh.lvl_len = 1;
+      sl.pend[0] = 0;
+      sl.pend[1] = 1;
+    }
+    team_sync<TEAM>();
+    nlev = 1;
+    uint32_t l0 = 0, l1 = 1;
+    for (;;) {
+      expand_forward<D, TEAM, PACKED, WALK_KAHN>(a, out_rows(a.g), sl, sh, sl.ends, l0, l1, s, t, INF, relax,
+                                                 scanned);
+      const uint32_t l2 = sh.lvl_len;
+      if (l2 == l1) break;
+      if (t == 0) sl.pend[nlev + 1] = l2;
+      ++nlev;
+      l0 = l1;
+      l1 = l2;
+    }
+    team_sync<TEAM>();
+    cyc_settle += clock64() - c0;
+    if (l1 != nr) err = DEV_ERR_INTERNAL;  // every reached vertex must be released exactly once
+  }
+  if (err != DEV_OK) {
+    if (t == 0) atomicCAS(a.err, DEV_OK, err);
+    for (uint32_t j = t; j < nr; j += TEAM) {
+      const uint32_t v = ldcg(&sl.S[j]);
+      sl.d[v] = INF;
+      sl.pc[v] = 0;
+    }
+  } else if (a.flags & RUN_FORWARD_ONLY) {
+    // test hook: present the levels in the S / ends layout of the strict schedule
+    for (uint32_t j = t; j < nr; j += TEAM) sl.S[j] = ldcg(&sl.ends[j]);
+    team_sync<TEAM>();
+    for (uint32_t l = t; l <= nlev; l += TEAM) sl.ends[l] = ldcg(&sl.pend[l]);
+    if (t == 0 && a.debug_out) {
+      a.debug_out[0] = nlev;
+      a.debug_out[1] = nr;
+    }
+  } else {
+    c0 = clock64();
+    const int last = a.ebc ? 0 : 1;
+    for (int lev = (int)nlev - 1; lev >= last; --lev) {
+      const uint32_t b0 = ldcg(&sl.pend[lev]);
+      const uint32_t b1 = ldcg(&sl.pend[lev + 1]);
+      accumulate_level<D, TEAM, PACKED>(a, sl, sh, sl.ends, b0, b1, s, t, scanned);
+    }
+    cyc_back += clock64() - c0;
+    for (uint32_t j = t; j < nr; j += TEAM) sl.d[ldcg(&sl.S[j])] = INF;
+  }
+  if (a.stats) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      relax += __shfl_xor_sync(FULL, relax, o);
+      scanned += __shfl_xor_sync(FULL, scanned, o);
+    }
+    if ((t & 31) == 0) {
+      atomicAdd(&a.stats[STAT_RELAX], relax);
+      atomicAdd(&a.stats[STAT_ENTRIES], scanned);
+    }
+    if (t == 0) {
+      atomicAdd(&a.stats[STAT_SOURCES], 1ull);
+      atomicAdd(&a.stats[STAT_PHASES], (unsigned long long)rounds);
+      atomicAdd(&a.stats[STAT_REFILLS], (unsigned long long)advances);
+      atomicAdd(&a.stats[STAT_REACHED], (unsigned long long)nr);
+      atomicAdd(&a.stats[STAT_LEVELS], (unsigned long long)nlev);
+      atomicAdd(&a.stats[STAT_CYC_EXPAND], cyc_expand);
+      atomicAdd(&a.stats[STAT_CYC_REFILL], cyc_refill);
+      atomicAdd(&a.stats[STAT_CYC_SETTLE], cyc_settle);
+      atomicAdd(&a.stats[STAT_CYC_BACKWARD], cyc_back);
+      atomicAdd(&a.stats[STAT_FAR_SCANNED], far_sc);
+    }
+  }
+  team_sync<TEAM>();
+  return err == DEV_OK;
+}
+
+// One instantiation per schedule, so the strict schedule's register allocation
+// does not pay for the delta-stepping code.
+template <typename D, int TEAM, int BLOCK, bool PACKED, int ALGO>
 __global__ void __launch_bounds__(BLOCK) bc_batched_kernel(const BatchArgs a) {
   static_assert(TEAM == 32 || TEAM == BLOCK, "a CTA holds either warp teams or one team");
   constexpr int NTEAMS = BLOCK / TEAM;
@@ -968,14 +1215,21 @@ __global__ void __launch_bounds__(BLOCK) bc_batched_kernel(const BatchArgs a) {
       continue;
     }
     if (a.g.o2n) s = __ldg(&a.g.o2n[s]);
-    const bool ok = run_source<D, TEAM, PACKED>(a, sl, sh, s, t);
+    bool ok;
+    if constexpr (ALGO == ALGO_DELTA)
+      ok = run_source_ds<D, TEAM, PACKED>(a, sl, sh, s, t);
+    else
+      ok = run_source<D, TEAM, PACKED>(a, sl, sh, s, t);
     if (!ok || (a.flags & RUN_FORWARD_ONLY)) break;
   }
 }
 
 template <typename D, int TEAM, int BLOCK, bool PACKED>
 cudaError_t launch_t(const BatchArgs& a, int grid, cudaStream_t st) {
-  bc_batched_kernel<D, TEAM, BLOCK, PACKED><<<grid, BLOCK, 0, st>>>(a);
+  if (a.algo == ALGO_DELTA)
+    bc_batched_kernel<D, TEAM, BLOCK, PACKED, ALGO_DELTA><<<grid, BLOCK, 0, st>>>(a);
+  else
+    bc_batched_kernel<D, TEAM, BLOCK, PACKED, ALGO_STRICT><<<grid, BLOCK, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -990,15 +1244,20 @@ cudaError_t launch_d(const BatchArgs& a, int team, int grid, cudaStream_t st) {
   }
 }
 
-template <typename D, bool PACKED>
-cudaError_t occ_d(int team, int* out) {
+template <typename D, bool PACKED, int ALGO>
+cudaError_t occ_a(int team, int* out) {
   switch (team) {
-    case 32: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, bc_batched_kernel<D, 32, 256, PACKED>, 256, 0);
-    case 128: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, bc_batched_kernel<D, 128, 128, PACKED>, 128, 0);
-    case 256: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, bc_batched_kernel<D, 256, 256, PACKED>, 256, 0);
-    case 512: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, bc_batched_kernel<D, 512, 512, PACKED>, 512, 0);
+    case 32: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, bc_batched_kernel<D, 32, 256, PACKED, ALGO>, 256, 0);
+    case 128: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, bc_batched_kernel<D, 128, 128, PACKED, ALGO>, 128, 0);
+    case 256: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, bc_batched_kernel<D, 256, 256, PACKED, ALGO>, 256, 0);
+    case 512: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, bc_batched_kernel<D, 512, 512, PACKED, ALGO>, 512, 0);
     default: return cudaErrorInvalidValue;
   }
+}
+
+template <typename D, bool PACKED>
+cudaError_t occ_d(int team, int algo, int* out) {
+  return algo == ALGO_DELTA ? occ_a<D, PACKED, ALGO_DELTA>(team, out) : occ_a<D, PACKED, ALGO_STRICT>(team, out);
 }
 
 }  // namespace
@@ -1015,13 +1274,17 @@ cudaError_t launch_batched(const BatchArgs& a, int dist_bits, int team, int grid
 }
 
 // Resident CTAs per SM; for 32-bit distances the smaller of the two adjacency forms.
-cudaError_t batched_occupancy(int dist_bits, int team, int* blocks_per_sm) {
-  if (dist_bits != 32) return occ_d<uint64_t, false>(team, blocks_per_sm);
+cudaError_t batched_occupancy(int dist_bits, int team, int algo, int* blocks_per_sm) {
+  if (dist_bits != 32) return occ_d<uint64_t, false>(team, algo, blocks_per_sm);
   int a = 0, b = 0;
-  cudaError_t e = occ_d<uint32_t, false>(team, &a);
-  if (e == cudaSuccess) e = occ_d<uint32_t, true>(team, &b);
+  cudaError_t e = occ_d<uint32_t, false>(team, algo, &a);
+  if (e == cudaSuccess) e = occ_d<uint32_t, true>(team, algo, &b);
   *blocks_per_sm = a < b ? a : b;
   return e;
+}
+
+cudaError_t batched_occupancy(int dist_bits, int team, int* blocks_per_sm) {
+  return batched_occupancy(dist_bits, team, ALGO_STRICT, blocks_per_sm);
 }
 
 }  // namespace bcgpu

@@ -43,10 +43,11 @@ struct GraphDev {
 // (zero between sources); pend: end of each level's range in the DAG edge
 // list; pairs: the shortest-path DAG edges (u -> v) found while pulling sigma,
 // in level order of v (capacity pair_cap; on overflow the backward pass falls
-// back to scanning every CSR entry).
+// back to scanning every CSR entry); pc: per-vertex round stamps, then
+// predecessor counts, of the delta-stepping schedule (zero between sources).
 struct SlabLayout {
   uint64_t stride;
-  uint64_t off_d, off_sig, off_S, off_ends, off_near, off_far, off_far2, off_acc, off_pend, off_pairs;
+  uint64_t off_d, off_sig, off_S, off_ends, off_near, off_far, off_far2, off_acc, off_pend, off_pairs, off_pc;
   uint32_t pair_cap;
 };
 
@@ -54,10 +55,17 @@ enum : uint32_t {
   RUN_FORWARD_ONLY = 1u,  // stop after distances / sigma / levels (test hook)
 };
 
+// Per-source schedules of the batched kernel.
+enum : uint32_t {
+  ALGO_STRICT = 1,  // strict settle batches (Sec. 3.2), sigma pulled per batch
+  ALGO_DELTA = 2,   // delta-stepping distances, then sigma and delta over DAG hop levels
+};
+
 enum : int {
   DEV_OK = 0,
   DEV_ERR_INVALID = 1,  // out-of-range source
   DEV_ERR_TIMEOUT = 4,  // phase cap hit
+  DEV_ERR_INTERNAL = 5, // a consistency check failed (reported as BC_ERR_CUDA)
 };
 
 // Per-run counters (summed over sources).
@@ -76,6 +84,7 @@ enum : int {
   STAT_CYC_BACKWARD,
   STAT_NEAR_SCANNED,  // near / far queue entries read by the threshold, settle and refill passes
   STAT_FAR_SCANNED,
+  STAT_LEVELS,        // levels of the backward pass
   STAT_COUNT
 };
 
@@ -97,6 +106,7 @@ struct BatchArgs {
   uint32_t warp_deg;   // forward expansion: rows with >= warp_deg entries get a warp each
   uint32_t team_deg;   // ... and rows with >= team_deg entries the whole team
   uint32_t hot_n;      // ids below hot_n are gathered with an L2 evict-last hint
+  uint32_t algo;       // ALGO_*
   uint32_t flags;      // RUN_*
   uint32_t* debug_out; // RUN_FORWARD_ONLY: [0] = levels, [1] = reached
 };
@@ -104,7 +114,8 @@ struct BatchArgs {
 // Launchers (bc_batched.cu).  team: 32, 128, 256 or 512 threads per source.
 cudaError_t launch_batched(const BatchArgs& a, int dist_bits, int team, int grid, cudaStream_t st);
 int batched_block_threads(int team);
-cudaError_t batched_occupancy(int dist_bits, int team, int* blocks_per_sm);
+cudaError_t batched_occupancy(int dist_bits, int team, int* blocks_per_sm);  // strict schedule
+cudaError_t batched_occupancy(int dist_bits, int team, int algo, int* blocks_per_sm);
 
 // Graph preparation and small helpers (bc_prep.cu).
 cudaError_t launch_prep(uint32_t n, uint64_t nnz, const uint64_t* row_ptr, const uint32_t* col, const uint32_t* w,

@@ -77,6 +77,8 @@ SlabLayout na_layout(uint32_t n) {
   L.pair_cap = (uint32_t)std::min<uint64_t>(2ull * n + 64, 0xffffffffull);
   L.off_pairs = off;
   off += al256((uint64_t)L.pair_cap * 8);
+  L.off_pc = off;
+  off += al256((uint64_t)n * 4);
   L.stride = off;
   return L;
 }
@@ -192,6 +194,8 @@ extern "C" int bc_compute_noalloc(const uint64_t* d_row_ptr, const uint32_t* d_c
                                               0xffffffffu, st);
   if (e == cudaSuccess)
     e = launch_fill_slabs(slabs, lay.stride, (uint32_t)slots, lay.off_acc, al256((uint64_t)n * 8), 0u, st);
+  if (e == cudaSuccess)
+    e = launch_fill_slabs(slabs, lay.stride, (uint32_t)slots, lay.off_pc, al256((uint64_t)n * 4), 0u, st);
   if (e == cudaSuccess) {
     BatchArgs a{};
     a.g.n = n;
@@ -215,6 +219,7 @@ extern "C" int bc_compute_noalloc(const uint64_t* d_row_ptr, const uint32_t* d_c
     a.stats = ctl->stats;
     a.flags = 0;
     a.debug_out = ctl->debug;
+    a.algo = ALGO_STRICT;
     a.warp_deg = cfg.warp_degree ? cfg.warp_degree : 32u;
     a.team_deg = std::max<uint32_t>(cfg.team_degree ? cfg.team_degree : 8u * team, a.warp_deg);
     const int grid = (int)((slots + per_block - 1) / per_block);
