@@ -51,7 +51,7 @@ WORKLOADS = {
 # per reached vertex 80 B.
 BYTES_PER_ENTRY = 64
 BYTES_PER_VERTEX = 80
-KERNEL_SRC = os.path.join(ROOT, "paper_1701_05975_gb300", "csrc", "bc_batched.cu")
+KERNEL_SRC = os.path.join(ROOT, "paper_1701_05975_gb300", "csrc", "bc_batched.cuh")
 
 
 def reach_model(g, sources):

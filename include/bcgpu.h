@@ -91,7 +91,8 @@ typedef uint64_t bc_request_t;
  */
 typedef struct bc_config {
   uint32_t mode;          /* BC_MODE_BATCHED or BC_MODE_PLAIN */
-  uint32_t team_threads;  /* threads that share one source: 32 (warp team) or 128/256/512 (CTA team) */
+  uint32_t team_threads;  /* threads that share one source: 32 (warp team) or 128/256/512/1024 (CTA team);
+                             1024 needs 32-bit distances and falls back to 512 otherwise */
   uint32_t max_slots;     /* cap on sources in flight at once (per-source slabs held in device memory) */
   uint32_t settle_in;     /* 1: settle by the strict OUT criterion (Eq. 2 + Eq. 4) OR the strict IN
                              criterion; 2: OUT only (the paper's criterion alone); 0 = automatic (1) */
@@ -101,6 +102,8 @@ typedef struct bc_config {
   uint32_t warp_degree;   /* forward expansion: rows with at least this many entries get one warp each */
   uint32_t team_degree;   /* ... and rows with at least this many entries the whole team (>= warp_degree) */
   uint32_t algorithm;     /* BC_ALGO_AUTO, BC_ALGO_STRICT or BC_ALGO_DELTA (batched mode) */
+  uint32_t hot_vertices;  /* on degree-relabeled graphs, the distance words of this many leading (highest-
+                             degree) vertex ids are gathered with an L2 evict-last hint; 0 = automatic */
 } bc_config;
 
 /* Read the current process-wide configuration. */

@@ -49,7 +49,7 @@ class bc_config(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_uint32), ("team_threads", ctypes.c_uint32), ("max_slots", ctypes.c_uint32),
                 ("settle_in", ctypes.c_uint32), ("bucket_width", ctypes.c_uint64), ("phase_cap", ctypes.c_uint64),
                 ("mem_fraction", ctypes.c_double), ("warp_degree", ctypes.c_uint32), ("team_degree", ctypes.c_uint32),
-                ("algorithm", ctypes.c_uint32)]
+                ("algorithm", ctypes.c_uint32), ("hot_vertices", ctypes.c_uint32)]
 
 
 class bc_graph_info(ctypes.Structure):

@@ -207,6 +207,11 @@ void ws_free(Workspace* w) {
 
 // Settings for a run: explicit config fields win, then the graph's tuned
 // values, then heuristics.
+// Default L2 evict-last prefix (vertex ids after degree relabeling).
+#ifndef BCGPU_HOT_VERTICES
+#define BCGPU_HOT_VERTICES 32768u
+#endif
+
 struct RunCfg {
   uint32_t team;
   uint64_t width;
@@ -218,6 +223,7 @@ struct RunCfg {
   uint32_t warp_deg;
   uint32_t team_deg;
   uint32_t algo;  // ALGO_STRICT or ALGO_DELTA
+  uint32_t hot_n;
 };
 
 RunCfg resolve(const bc_graph* g) {
@@ -225,10 +231,14 @@ RunCfg resolve(const bc_graph* g) {
   RunCfg r;
   r.mode = c.mode;
   const double avg_deg = g->n ? (double)g->nnz / g->n : 0.0;
-  // measured defaults: wide CTA teams for dense skewed graphs (large
-  // frontiers per batch), 128-thread teams for sparse high-diameter graphs
-  const uint32_t team_default = avg_deg >= 20.0 ? 512u : (avg_deg >= 6.0 ? 256u : 128u);
+  // measured defaults: the widest CTA teams for dense skewed graphs (large
+  // frontiers per batch; half as many sources in flight keeps more of each
+  // source's distance array in L2), 128-thread teams for sparse high-diameter
+  // graphs
+  const uint32_t wide = g->dist_bits == 32 ? 1024u : 512u;
+  const uint32_t team_default = avg_deg >= 20.0 ? wide : (avg_deg >= 6.0 ? 256u : 128u);
   r.team = c.team_threads ? c.team_threads : (g->tuned.team ? g->tuned.team : team_default);
+  if (r.team == 1024 && g->dist_bits != 32) r.team = 512;  // 1024-thread teams hold 32-bit distances only
   r.width = c.bucket_width ? c.bucket_width
                            : (g->tuned.width ? g->tuned.width : std::max<uint64_t>(1, g->max_w / 4));
   uint32_t si = c.settle_in ? c.settle_in : (g->tuned.settle_in ? g->tuned.settle_in : 1u);
@@ -241,6 +251,8 @@ RunCfg resolve(const bc_graph* g) {
   r.team_deg = std::max(r.team_deg, r.warp_deg);
   const uint32_t al = c.algorithm ? c.algorithm : (g->tuned.algo ? g->tuned.algo : (uint32_t)BC_ALGO_STRICT);
   r.algo = (al == BC_ALGO_DELTA) ? ALGO_DELTA : ALGO_STRICT;
+  const uint32_t hot = c.hot_vertices ? c.hot_vertices : BCGPU_HOT_VERTICES;
+  r.hot_n = g->relabeled ? std::min<uint32_t>(g->n, hot) : 0u;
   return r;
 }
 
@@ -353,7 +365,7 @@ BatchArgs make_args(bc_graph* g, Workspace* w, const RunCfg& r, const uint32_t* 
   a.algo = r.algo;
   // the highest-degree vertices after relabeling: 128 KiB of 32-bit distance
   // words per source (the whole L2 holds this prefix for ~1000 sources)
-  a.hot_n = g->relabeled ? std::min<uint32_t>(g->n, 32768u) : 0u;
+  a.hot_n = r.hot_n;
   return a;
 }
 
@@ -607,8 +619,8 @@ int bc_set_config(const bc_config* cfg) {
   if (!cfg) return fail(BC_ERR_INVALID, "null config");
   if (cfg->mode != BC_MODE_BATCHED && cfg->mode != BC_MODE_PLAIN) return fail(BC_ERR_INVALID, "bad mode");
   if (cfg->team_threads && cfg->team_threads != 32 && cfg->team_threads != 128 && cfg->team_threads != 256 &&
-      cfg->team_threads != 512)
-    return fail(BC_ERR_INVALID, "team_threads must be 0, 32, 128, 256 or 512");
+      cfg->team_threads != 512 && cfg->team_threads != 1024)
+    return fail(BC_ERR_INVALID, "team_threads must be 0, 32, 128, 256, 512 or 1024");
   if (cfg->settle_in > 2) return fail(BC_ERR_INVALID, "settle_in must be 0, 1 or 2");
   if (cfg->algorithm > BC_ALGO_DELTA) return fail(BC_ERR_INVALID, "algorithm must be 0, 1 or 2");
   if (cfg->mem_fraction < 0 || cfg->mem_fraction > 0.95) return fail(BC_ERR_INVALID, "mem_fraction out of range");
@@ -1051,7 +1063,8 @@ int bc_autotune(bc_graph_t g, const uint32_t* sources, uint32_t k_probe) {
   CK(cudaSetDevice(g->device));
   bc_config user = config_snapshot();
   // candidates: team size x near/far split width, then sources in flight
-  const uint32_t teams[] = {128, 256, 512};
+  std::vector<uint32_t> teams = {128, 256, 512};
+  if (g->dist_bits == 32) teams.push_back(1024);
   std::vector<uint64_t> widths;
   for (uint64_t d : {16ull, 4ull, 1ull}) {
     const uint64_t wv = std::max<uint64_t>(1, g->max_w / d);

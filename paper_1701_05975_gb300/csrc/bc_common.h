@@ -116,6 +116,8 @@ cudaError_t launch_batched(const BatchArgs& a, int dist_bits, int team, int grid
 int batched_block_threads(int team);
 cudaError_t batched_occupancy(int dist_bits, int team, int* blocks_per_sm);  // strict schedule
 cudaError_t batched_occupancy(int dist_bits, int team, int algo, int* blocks_per_sm);
+cudaError_t launch_batched_delta(const BatchArgs& a, int dist_bits, int team, int grid, cudaStream_t st);
+cudaError_t batched_occupancy_delta(int dist_bits, int team, int* blocks_per_sm);
 
 // Graph preparation and small helpers (bc_prep.cu).
 cudaError_t launch_prep(uint32_t n, uint64_t nnz, const uint64_t* row_ptr, const uint32_t* col, const uint32_t* w,

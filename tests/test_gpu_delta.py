@@ -60,6 +60,7 @@ CONFIGS = [
     dict(team_threads=128, bucket_width=0),
     dict(team_threads=256, bucket_width=7),
     dict(team_threads=512, bucket_width=1 << 40),
+    dict(team_threads=1024, bucket_width=30),
 ]
 
 

@@ -47,6 +47,7 @@ CONFIGS = [
     dict(team_threads=128, settle_in=2, bucket_width=1),
     dict(team_threads=256, settle_in=1, bucket_width=3),
     dict(team_threads=512, settle_in=2, bucket_width=1 << 40),
+    dict(team_threads=1024, settle_in=1, bucket_width=2),
 ]
 
 
@@ -112,7 +113,7 @@ def test_levels_are_legal_and_distances_exact_on_er1k():
             assert np.all(lev[rows[dag]] < lev[cols[dag]])
 
 
-@pytest.mark.parametrize("team", [32, 128, 256, 512])
+@pytest.mark.parametrize("team", [32, 128, 256, 512, 1024])
 def test_er1k_workload_full(team):
     bc.bc_set_config(team_threads=team)
     g, src, scale = gen.workload_er1k()
@@ -249,6 +250,8 @@ def test_dag_edge_list_overflow_falls_back_to_entry_scan():
 
 
 def test_wide_weights_use_unpacked_entries_and_64bit_distances():
+    # 1024-thread teams hold 32-bit distances only: the request falls back to 512
+    bc.bc_set_config(team_threads=1024)
     rng = np.random.default_rng(55)
     for i in range(10):
         n = int(rng.integers(2, 200))
@@ -258,6 +261,8 @@ def test_wide_weights_use_unpacked_entries_and_64bit_distances():
             if g.nnz:
                 assert G.info().dist_bits == 64
             assert_bc_close(G.compute(src, 1.0), oracle.bc(g, src, 1.0))
+            if g.nnz:
+                assert G.stats().team_threads == 512
             d, sg, _ = G.sssp_debug(0)
             d_ref, sg_ref, _ = oracle.sssp(g, 0)
             assert np.array_equal(d, d_ref) and np.array_equal(sg, sg_ref)
