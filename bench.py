@@ -358,6 +358,15 @@ def run_serving(args, desc):
     makespan, st = run_stream(reqs, rate)
     edges = sum(len(r.sources) * pool[(r.kind, r.n)].m for r in reqs)
     gteps = edges / makespan / 1e9
+    # optional load sweep: shorter streams (the first --sweep-requests
+    # requests) at other fractions of the saturated rate
+    sweep = []
+    for load in ([float(x) for x in args.sweep.split(",")] if args.sweep else []):
+        sub = reqs[: args.sweep_requests]
+        mk, sst = run_stream(sub, load * sat_rate)
+        e = sum(len(r.sources) * pool[(r.kind, r.n)].m for r in sub)
+        sweep.append({"load": load, "requests": len(sub), "gteps": e / mk / 1e9, "p50_ms": sst.p50_ms,
+                      "p99_ms": sst.p99_ms, "mean_ms": sst.mean_ms})
     line = {
         "metric": "serving: aggregate GTEPS and p50/p99 latency (submit -> done)", "value": gteps, "unit": "GTEPS",
         "n_gpus": ws, "steps": 1, "warmup": 1, "ms_per_step": makespan * 1e3, "higher_is_better": True,
@@ -366,6 +375,7 @@ def run_serving(args, desc):
                    "saturated_rate_per_s": sat_rate, "load": 0.7},
         "latency_ms": {"p50": st.p50_ms, "p99": st.p99_ms, "mean": st.mean_ms},
         "completed": int(st.completed), "failed": int(st.failed), "max_concurrent": int(st.max_concurrent),
+        "sweep": sweep,
         "e2e": {"value": gteps, "unit": "GTEPS", "h2d_bytes_per_step": int(sum(4 * len(r.sources) for r in reqs)),
                 "d2h_bytes_per_step": int(sum(8 * r.n for r in reqs))},
     }
@@ -388,6 +398,8 @@ def main():
     ap.add_argument("--autotune", type=int, default=-1,
                     help="probe sources for the autotuner (-1: automatic size, 0: off)")
     ap.add_argument("--requests", type=int, default=2000, help="serving workload: number of requests")
+    ap.add_argument("--sweep", default="", help="serving workload: extra loads, e.g. 0.3,0.5,0.9 (default: none)")
+    ap.add_argument("--sweep-requests", type=int, default=300, help="serving workload: requests per sweep load")
     ap.add_argument("--sources", type=int, default=0,
                     help="use only the first K sources of the workload (small profiling cases); 0 = all")
     ap.add_argument("--max-slots", type=int, default=0, help="cap on sources in flight (0 = automatic)")
