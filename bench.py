@@ -403,6 +403,8 @@ def main():
     ap.add_argument("--sources", type=int, default=0,
                     help="use only the first K sources of the workload (small profiling cases); 0 = all")
     ap.add_argument("--max-slots", type=int, default=0, help="cap on sources in flight (0 = automatic)")
+    ap.add_argument("--no-graph", action="store_true", help="enqueue each step with bc_compute_async instead of "
+                    "replaying a captured step graph")
     args = ap.parse_args()
 
     desc, maker = WORKLOADS[args.workload]
@@ -456,13 +458,26 @@ def main():
     d_out = torch.empty(g.n, dtype=torch.float64, device=dev)
     k = len(sources)
 
+    # a step is one batched run over all sources, captured once as a CUDA
+    # graph (bc_step_create) and replayed; --no-graph enqueues it call by call
+    step_h = None if args.no_graph else bc.bc_step_create(G.handle, d_src.data_ptr(), k, scale, d_out.data_ptr())
+
     def step():
-        bc.bc_compute_async(G.handle, d_src.data_ptr(), k, scale, d_out.data_ptr(), stream.cuda_stream)
+        if step_h is not None:
+            bc.bc_step_launch(step_h, stream.cuda_stream)
+        else:
+            bc.bc_compute_async(G.handle, d_src.data_ptr(), k, scale, d_out.data_ptr(), stream.cuda_stream)
+
+    def sync_status():
+        if step_h is not None:
+            bc.bc_step_sync(step_h, stream.cuda_stream)
+        else:
+            bc.bc_sync_status(G.handle, stream.cuda_stream)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             step()
-        bc.bc_sync_status(G.handle, stream.cuda_stream)
+        sync_status()
     st = G.stats()
     barrier()
     torch.cuda.synchronize(dev)
@@ -479,7 +494,7 @@ def main():
             ev[i][1].record(stream)
         t_end.record(stream)
     torch.cuda.synchronize(dev)
-    bc.bc_sync_status(G.handle, stream.cuda_stream)
+    sync_status()
     barrier()
     clk = clocks.stop()
     total_ms = t_start.elapsed_time(t_end)
@@ -525,6 +540,7 @@ def main():
                    "team_threads": int(st.team_threads), "slots": int(st.slots),
                    "bucket_width": int(st.bucket_width), "parallelism": f"replicas x{ws}",
                    "autotune": {"probe_sources": probe, "seconds": round(tune_s, 2)},
+                   "launch": "bc_compute_async per step" if args.no_graph else "CUDA graph (bc_step_launch)",
                    "relabeled_by_degree": bool(G.info().relabeled), "dist_bits": int(G.info().dist_bits)},
         "e2e": {"value": ws * k * m / e2e_s / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": 4 * k,
                 "d2h_bytes_per_step": 8 * g.n},
@@ -552,6 +568,8 @@ def main():
         line["cpu_baseline"] = cpu_baseline(g, sources)
     if rank == 0:
         print(json.dumps(line), flush=True)
+    if step_h is not None:
+        bc.bc_step_destroy(step_h)
     G.close()
     if dist is not None:
         dist.destroy_process_group()

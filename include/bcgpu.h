@@ -281,6 +281,30 @@ int bc_last_run_stats(bc_graph_t g, bc_run_stats *out);
 int bc_autotune(bc_graph_t g, const uint32_t *sources, uint32_t k_probe);
 
 /*
+ * Step graphs: one batched run (Algorithms 1-3 for every source of a fixed
+ * list, Sec. 3.1's block-per-source batching) captured once as a CUDA graph
+ * and replayed with a single launch.  The step is bound to DEVICE buffers
+ * that the caller owns and keeps alive until bc_step_destroy: d_sources[k]
+ * (read at every launch, so the caller may rewrite the ids in place between
+ * launches) and d_out_bc[n] (zeroed, accumulated and scaled at every launch,
+ * caller's vertex ids).  The configuration (team size, width, schedule, slots)
+ * is the one in effect at creation.  The step owns its workspace: launches of
+ * one step must be ordered (one stream, or caller-ordered streams); different
+ * steps run concurrently.  bc_step_launch returns once the graph is enqueued
+ * on `stream` (a cudaStream_t, NULL = legacy default); bc_step_sync waits for
+ * the stream and returns the device status of the last launch (BC_ERR_INVALID
+ * for a source >= n, BC_ERR_TIMEOUT for a phase cap hit; the step stays usable)
+ * and records bc_last_run_stats.  bc_graph_destroy fails with BC_ERR_BUSY
+ * while steps of the graph exist.
+ */
+typedef struct bc_step *bc_step_t;
+int bc_step_create(bc_graph_t g, const uint32_t *d_sources, uint32_t k, double scale, double *d_out_bc,
+                   bc_step_t *out);
+int bc_step_launch(bc_step_t step, void *stream);
+int bc_step_sync(bc_step_t step, void *stream);
+int bc_step_destroy(bc_step_t step);
+
+/*
  * No-allocation variant of bc_compute_async, for callers that cannot allocate
  * device memory while they run (a host thread with real-time limits, code
  * running while another framework owns the device allocator, a process whose

@@ -167,6 +167,7 @@ struct bc_graph {
   std::unordered_map<cudaStream_t, Workspace*> async_ws;
   bc_run_stats last{};
   std::atomic<int> serving_refs{0};
+  std::atomic<int> step_refs{0};
   PlainWork* plain = nullptr;
   PaperWork* paper = nullptr;
   cudaStream_t stream = nullptr;  // internal stream of the synchronous calls
@@ -827,6 +828,7 @@ int bc_graph_create(const uint64_t* row_ptr, const uint32_t* col_idx, const uint
 int bc_graph_destroy(bc_graph_t g) {
   if (int rc = check_graph(g)) return rc;
   if (g->serving_refs.load() > 0) return fail(BC_ERR_BUSY, "graph still has serving requests");
+  if (g->step_refs.load() > 0) return fail(BC_ERR_BUSY, "graph still has step graphs (bc_step_destroy them first)");
   cudaSetDevice(g->device);
   cudaStreamSynchronize(g->stream);
   for (auto& w : g->pool) {
@@ -1151,6 +1153,116 @@ int bc_autotune(bc_graph_t g, const uint32_t* sources, uint32_t k_probe) {
   g->tuned = best;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune_cache[g->fingerprint] = best;
+  return BC_OK;
+}
+
+// ---- step graphs --------------------------------------------------------
+
+}  // extern "C"
+
+struct bc_step {
+  bc_graph* g = nullptr;
+  Workspace ws;  // private: never in the graph's pool
+  RunCfg r{};
+  uint32_t slots = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+void step_free(bc_step* s) {
+  if (s->exec) cudaGraphExecDestroy(s->exec);
+  if (s->graph) cudaGraphDestroy(s->graph);
+  ws_free(&s->ws);
+}
+
+}  // namespace
+
+extern "C" {
+
+int bc_step_create(bc_graph_t g, const uint32_t* d_sources, uint32_t k, double scale, double* d_out_bc,
+                   bc_step_t* out) {
+  if (!out) return fail(BC_ERR_INVALID, "null output handle");
+  *out = nullptr;
+  if (int rc = check_graph(g)) return rc;
+  if (!d_out_bc) return fail(BC_ERR_INVALID, "null d_out_bc");
+  if (k && !d_sources) return fail(BC_ERR_INVALID, "null d_sources");
+  CK(cudaSetDevice(g->device));
+  RunCfg r = resolve(g);
+  if (r.mode != BC_MODE_BATCHED) return fail(BC_ERR_INVALID, "step graphs capture the batched mode only");
+  auto s = std::make_unique<bc_step>();
+  s->g = g;
+  s->r = r;
+  if (int rc = plan_slots(g, r, k, &s->slots)) return rc;
+  Workspace& w = s->ws;
+  w.slots = s->slots;
+  w.lay = make_layout(g->n, g->dist_bits);
+  w.bytes = w.lay.stride * s->slots;
+  cudaStream_t cap = nullptr;
+  cudaError_t e = cudaMalloc(&w.slabs, w.bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&w.ctl, sizeof(Ctl));
+  if (e == cudaSuccess) e = cudaMallocHost(&w.host_ctl, sizeof(Ctl));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  // the slab invariant, established once: later runs restore it themselves
+  if (e == cudaSuccess)
+    e = launch_fill_slabs(w.slabs, w.lay.stride, s->slots, w.lay.off_d,
+                          align256((uint64_t)g->n * (g->dist_bits / 8)), 0xffffffffu, cap);
+  if (e == cudaSuccess)
+    e = launch_fill_slabs(w.slabs, w.lay.stride, s->slots, w.lay.off_acc, align256((uint64_t)g->n * 8), 0u, cap);
+  if (e == cudaSuccess)
+    e = launch_fill_slabs(w.slabs, w.lay.stride, s->slots, w.lay.off_pc, align256((uint64_t)g->n * 4), 0u, cap);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cap);
+  if (e != cudaSuccess) {
+    if (cap) cudaStreamDestroy(cap);
+    step_free(s.get());
+    return cuda_fail(e, "step workspace");
+  }
+  // capture: zero control block and output, source check, persistent kernel,
+  // scale, status copy to pinned host memory
+  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  int rc = BC_OK;
+  if (e == cudaSuccess) {
+    rc = enqueue_batched(g, &w, r, d_sources, k, scale, d_out_bc, nullptr, s->slots, 0, cap, true);
+    if (!rc) {
+      cudaError_t e2 = cudaMemcpyAsync(w.host_ctl, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, cap);
+      if (e2 != cudaSuccess) rc = cuda_fail(e2, "cudaMemcpyAsync(control) during capture");
+    }
+    e = cudaStreamEndCapture(cap, &s->graph);  // always end the capture, also after a failed enqueue
+  }
+  if (e == cudaSuccess && !rc) e = cudaGraphInstantiate(&s->exec, s->graph, 0);
+  cudaStreamDestroy(cap);
+  if (rc || e != cudaSuccess) {
+    step_free(s.get());
+    return rc ? rc : cuda_fail(e, "step graph capture");
+  }
+  g->step_refs += 1;
+  *out = s.release();
+  return BC_OK;
+}
+
+int bc_step_launch(bc_step_t s, void* stream) {
+  if (!s) return fail(BC_ERR_INVALID, "null step handle");
+  CK(cudaSetDevice(s->g->device));
+  CK(cudaGraphLaunch(s->exec, static_cast<cudaStream_t>(stream)));
+  return BC_OK;
+}
+
+int bc_step_sync(bc_step_t s, void* stream) {
+  if (!s) return fail(BC_ERR_INVALID, "null step handle");
+  CK(cudaSetDevice(s->g->device));
+  CK(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  record_stats(s->g, *s->ws.host_ctl, s->r, s->slots);
+  return status_from_dev(s->ws.host_ctl->err);
+}
+
+int bc_step_destroy(bc_step_t s) {
+  if (!s) return fail(BC_ERR_INVALID, "null step handle");
+  cudaSetDevice(s->g->device);
+  cudaDeviceSynchronize();  // no launch of this step may still be in flight
+  s->g->step_refs -= 1;
+  step_free(s);
+  delete s;
   return BC_OK;
 }
 
