@@ -36,15 +36,35 @@ def run_async(G, n, sources, scale):
     return d_out.cpu().numpy()
 
 
-def check_workload(g, sources, scale, parts, n_oracle, n_debug):
+def run_step(G, n, sources, scale, launches=2):
+    """The benchmark's path: one batched run captured as a CUDA graph, replayed."""
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda:0")
+    d_src = torch.from_numpy(np.ascontiguousarray(sources, dtype=np.uint32).view(np.int32)).to(dev)
+    d_out = torch.empty(n, dtype=torch.float64, device=dev)
+    st = torch.cuda.Stream()
+    step = bc.bc_step_create(G.handle, d_src.data_ptr(), len(sources), scale, d_out.data_ptr())
+    try:
+        for _ in range(launches):
+            bc.bc_step_launch(step, st.cuda_stream)
+        bc.bc_step_sync(step, st.cuda_stream)
+    finally:
+        bc.bc_step_destroy(step)
+    return d_out.cpu().numpy()
+
+
+def check_workload(g, sources, scale, parts, n_oracle, n_debug, tune=False):
     with bc.Graph(g) as G:
-        full = run_async(G, g.n, sources, scale)
+        if tune:  # the benchmark tunes on a 2048-source probe before it times
+            G.autotune(sources[:2048])
+        full = run_step(G, g.n, sources, scale)
         stats = G.stats()
         assert stats.sources == len(sources) and stats.pair_overflows == 0
         total = np.zeros(g.n)
         for chunk in np.array_split(sources, parts):
             total += run_async(G, g.n, chunk, scale)
         assert_close(full, total, rel=1e-11)
+        assert_close(run_async(G, g.n, sources, scale), full, rel=1e-11)
         # oracle on a sample of sources that reach most of the graph
         deg = g.degrees()
         sample = [int(s) for s in sources if deg[s] > 0][:n_oracle]
@@ -56,12 +76,13 @@ def check_workload(g, sources, scale, parts, n_oracle, n_debug):
             d_ref, sg_ref, _ = oracle.sssp(g, s)
             assert np.array_equal(d, d_ref)
             assert np.array_equal(sg, sg_ref)
-        return full
+        return full, stats
 
 
 def test_rmat20_full_launch():
     g, sources, scale = gen.workload_rmat20()
-    full = check_workload(g, sources, scale, parts=4, n_oracle=6, n_debug=2)
+    full, stats = check_workload(g, sources, scale, parts=4, n_oracle=6, n_debug=2, tune=True)
+    assert stats.team_threads == 1024  # the configuration the benchmark measured
     # isolated vertices never lie on a path
     assert np.all(full[g.degrees() == 0] == 0)
 
