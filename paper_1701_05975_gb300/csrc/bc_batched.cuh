@@ -44,6 +44,16 @@ constexpr uint32_t NONE = 0xffffffffu;
 #define BCGPU_UNROLL 4
 #endif
 constexpr int UNROLL = BCGPU_UNROLL;  // independent edge loads in flight per thread
+// Settle stages the next batch's rows in shared memory (BCGPU_STAGE=0: off).
+#ifndef BCGPU_STAGE
+#define BCGPU_STAGE 1
+#endif
+// 1024-thread teams run one CTA per SM and take six (measured +1.4% on R-MAT;
+// six spills heavily in the smaller teams' register budget)
+template <int TEAM>
+__host__ __device__ constexpr int unroll_of() {
+  return TEAM >= 1024 ? 6 : UNROLL;
+}
 constexpr int NEAR_REGS = 4;          // near-queue entries per thread kept in registers
 constexpr uint64_t FAR_LEVELS = 16;   // the second far level starts FAR_LEVELS split widths out
 
@@ -124,6 +134,7 @@ struct TeamShared {
   Idx wlist[TEAM];
   Idx tlist[TEAM];
   uint32_t wnext, nwl, ntl;
+  uint32_t staged;  // leading entries of the next batch already in vtx / rs / dg / dv
   // delta-stepping schedule
   uint32_t front_len, def_len, lvl_len, round;
   uint32_t* front_out;
@@ -500,27 +511,28 @@ __device__ __forceinline__ void visit_entry(const Slab<D>& sl, TeamShared<D, TEA
 }
 
 // `lanes` threads (this one is number l) walk the whole row of chunk vertex i,
-// UNROLL independent adjacency loads and distance gathers in flight each.
+// unroll_of<TEAM>() independent adjacency loads and distance gathers in flight each.
 template <typename D, int TEAM, bool PACKED, int MODE>
 __device__ __forceinline__ void walk_row(const BatchArgs& a, const Rows& rows, const Slab<D>& sl,
                                          TeamShared<D, TEAM>& sh, uint32_t i, uint32_t l, uint32_t lanes, D split,
                                          unsigned long long& relax) {
+  constexpr int UNR = unroll_of<TEAM>();
   const D INF = dinf<D>();
   const uint64_t r0 = sh.rs[i];
   const uint32_t deg = sh.dg[i];
   const uint64_t pf = policy_evict_first(), pl = policy_evict_last();
-  for (uint32_t e0 = l; e0 < deg; e0 += lanes * UNROLL) {
-    uint2 ent[UNROLL];
+  for (uint32_t e0 = l; e0 < deg; e0 += lanes * UNR) {
+    uint2 ent[UNR];
 #pragma unroll
-    for (int q = 0; q < UNROLL; ++q) {
+    for (int q = 0; q < UNR; ++q) {
       const uint32_t e = e0 + q * lanes;
       ent[q] = e < deg ? load_entry<PACKED>(rows, r0 + e, pf) : make_uint2(0, 0);
     }
-    D dus[UNROLL];
+    D dus[UNR];
 #pragma unroll
-    for (int q = 0; q < UNROLL; ++q) dus[q] = (e0 + q * lanes < deg) ? gather_d(sl.d, ent[q].x, a.hot_n, pl) : INF;
+    for (int q = 0; q < UNR; ++q) dus[q] = (e0 + q * lanes < deg) ? gather_d(sl.d, ent[q].x, a.hot_n, pl) : INF;
 #pragma unroll
-    for (int q = 0; q < UNROLL; ++q)
+    for (int q = 0; q < UNR; ++q)
       if (e0 + q * lanes < deg) visit_entry<D, TEAM, MODE>(sl, sh, i, ent[q], dus[q], split, relax, a.hot_n, pl);
   }
 }
@@ -535,7 +547,8 @@ __device__ __forceinline__ void walk_row(const BatchArgs& a, const Rows& rows, c
 template <typename D, int TEAM, bool PACKED, int MODE>
 __device__ void expand_forward(const BatchArgs& a, const Rows& rows, const Slab<D>& sl, TeamShared<D, TEAM>& sh,
                                const uint32_t* list, uint32_t f0, uint32_t f1, uint32_t s, int t, D split,
-                               unsigned long long& relax, unsigned long long& scanned) {
+                               unsigned long long& relax, unsigned long long& scanned, uint32_t staged = 0) {
+  constexpr int UNR = unroll_of<TEAM>();
   const D INF = dinf<D>();
   const uint32_t warp_deg = a.warp_deg;
   const uint32_t team_deg = (TEAM == 32) ? a.warp_deg : a.team_deg;
@@ -543,15 +556,19 @@ __device__ void expand_forward(const BatchArgs& a, const Rows& rows, const Slab<
     const uint32_t cnt = min((uint32_t)TEAM, f1 - base);
     uint32_t deg = 0, small = 0, is_w = 0, is_t = 0;
     if ((uint32_t)t < cnt) {
-      const uint32_t v = ldcg(&list[base + t]);
-      const uint64_t r0 = __ldg(&rows.row_ptr[v]);
-      deg = (uint32_t)(__ldg(&rows.row_ptr[v + 1]) - r0);
-      sh.vtx[t] = v;
-      sh.rs[t] = r0;
-      sh.dg[t] = deg;
-      sh.dv[t] = ldcg(&sl.d[v]);
+      if (base == f0 && (uint32_t)t < staged) {
+        deg = sh.dg[t];  // placed by the settle step that formed this batch
+      } else {
+        const uint32_t v = ldcg(&list[base + t]);
+        const uint64_t r0 = __ldg(&rows.row_ptr[v]);
+        deg = (uint32_t)(__ldg(&rows.row_ptr[v + 1]) - r0);
+        sh.vtx[t] = v;
+        sh.rs[t] = r0;
+        sh.dg[t] = deg;
+        sh.dv[t] = ldcg(&sl.d[v]);
+      }
       sh.acc[t] = 0.0;
-      if (MODE == WALK_KAHN) sh.sv[t] = ldcg(&sl.sig[v]);
+      if (MODE == WALK_KAHN) sh.sv[t] = ldcg(&sl.sig[sh.vtx[t]]);
       if (deg >= team_deg) is_t = 1;
       else if (deg >= warp_deg) is_w = 1;
       else small = deg;
@@ -592,11 +609,11 @@ __device__ void expand_forward(const BatchArgs& a, const Rows& rows, const Slab<
     }
     // tier 1: short rows, edge-parallel over the whole team
     const uint64_t pf = policy_evict_first(), pl = policy_evict_last();
-    for (uint32_t e0 = t; e0 < total_small; e0 += TEAM * UNROLL) {
-      uint32_t iv[UNROLL];
-      uint2 ent[UNROLL];
+    for (uint32_t e0 = t; e0 < total_small; e0 += TEAM * UNR) {
+      uint32_t iv[UNR];
+      uint2 ent[UNR];
 #pragma unroll
-      for (int q = 0; q < UNROLL; ++q) {
+      for (int q = 0; q < UNR; ++q) {
         const uint32_t e = e0 + q * TEAM;
         iv[q] = NONE;
         ent[q] = make_uint2(0, 0);
@@ -605,11 +622,11 @@ __device__ void expand_forward(const BatchArgs& a, const Rows& rows, const Slab<
           ent[q] = load_entry<PACKED>(rows, sh.rs[iv[q]] + (e - sh.off[iv[q]]), pf);
         }
       }
-      D dus[UNROLL];
+      D dus[UNR];
 #pragma unroll
-      for (int q = 0; q < UNROLL; ++q) dus[q] = (iv[q] != NONE) ? gather_d(sl.d, ent[q].x, a.hot_n, pl) : INF;
+      for (int q = 0; q < UNR; ++q) dus[q] = (iv[q] != NONE) ? gather_d(sl.d, ent[q].x, a.hot_n, pl) : INF;
 #pragma unroll
-      for (int q = 0; q < UNROLL; ++q)
+      for (int q = 0; q < UNR; ++q)
         if (iv[q] != NONE) visit_entry<D, TEAM, MODE>(sl, sh, iv[q], ent[q], dus[q], split, relax, a.hot_n, pl);
     }
     team_sync<TEAM>();
@@ -629,18 +646,19 @@ template <typename D, int TEAM, bool PACKED>
 __device__ void accumulate_level(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, TEAM>& sh,
                                  const uint32_t* list, uint32_t f0, uint32_t f1, uint32_t s, int t,
                                  unsigned long long& scanned) {
+  constexpr int UNR = unroll_of<TEAM>();
   const D INF = dinf<D>();
   const bool edges = a.ebc != nullptr;
   for (uint32_t base = f0; base < f1; base += TEAM) {
     const uint32_t cnt = min((uint32_t)TEAM, f1 - base);
     const uint32_t total = load_chunk<D, TEAM>(a, sl, sh, list, base, cnt, t, edges);
     scanned += (t == 0) ? total : 0;
-    for (uint32_t e0 = t; e0 < total; e0 += TEAM * UNROLL) {
-      uint32_t iv[UNROLL];
-      uint64_t entry[UNROLL];
-      uint2 ent[UNROLL];
+    for (uint32_t e0 = t; e0 < total; e0 += TEAM * UNR) {
+      uint32_t iv[UNR];
+      uint64_t entry[UNR];
+      uint2 ent[UNR];
 #pragma unroll
-      for (int q = 0; q < UNROLL; ++q) {
+      for (int q = 0; q < UNR; ++q) {
         const uint32_t e = e0 + q * TEAM;
         iv[q] = NONE;
         entry[q] = 0;
@@ -651,11 +669,11 @@ __device__ void accumulate_level(const BatchArgs& a, const Slab<D>& sl, TeamShar
           ent[q] = load_entry<PACKED>(out_rows(a.g), entry[q], policy_evict_first());
         }
       }
-      D dus[UNROLL];
+      D dus[UNR];
 #pragma unroll
-      for (int q = 0; q < UNROLL; ++q) dus[q] = (iv[q] != NONE) ? ldcg(&sl.d[ent[q].x]) : INF;
+      for (int q = 0; q < UNR; ++q) dus[q] = (iv[q] != NONE) ? ldcg(&sl.d[ent[q].x]) : INF;
 #pragma unroll
-      for (int q = 0; q < UNROLL; ++q) {
+      for (int q = 0; q < UNR; ++q) {
         if (iv[q] == NONE) continue;
         const uint32_t i = iv[q];
         const D du = dus[q];
@@ -703,15 +721,16 @@ __device__ __forceinline__ void finalize_level(const BatchArgs& a, const Slab<D>
 template <int TEAM>
 __device__ __forceinline__ void push_level_pairs(const uint2* pairs, double* bacc, const double* sig, uint32_t p0,
                                                  uint32_t p1, int t) {
-  for (uint32_t p = p0 + t; p < p1; p += TEAM * UNROLL) {
-    uint2 pr[UNROLL];
+  constexpr int UNR = unroll_of<TEAM>();
+  for (uint32_t p = p0 + t; p < p1; p += TEAM * UNR) {
+    uint2 pr[UNR];
 #pragma unroll
-    for (int q = 0; q < UNROLL; ++q) pr[q] = (p + q * TEAM < p1) ? __ldcg(&pairs[p + q * TEAM]) : make_uint2(NONE, 0);
-    double c[UNROLL];
+    for (int q = 0; q < UNR; ++q) pr[q] = (p + q * TEAM < p1) ? __ldcg(&pairs[p + q * TEAM]) : make_uint2(NONE, 0);
+    double c[UNR];
 #pragma unroll
-    for (int q = 0; q < UNROLL; ++q) c[q] = (pr[q].x != NONE) ? __ldcg(&sig[pr[q].y]) : 0.0;
+    for (int q = 0; q < UNR; ++q) c[q] = (pr[q].x != NONE) ? __ldcg(&sig[pr[q].y]) : 0.0;
 #pragma unroll
-    for (int q = 0; q < UNROLL; ++q)
+    for (int q = 0; q < UNR; ++q)
       if (pr[q].x != NONE) atomicAdd(&bacc[pr[q].x], c[q]);
   }
 }
@@ -742,9 +761,13 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
     sh.stop = 0;
     sh.split = sat_add<D>((D)0, a.width);
     sh.split2 = sat_add<D>((D)0, (uint64_t)FAR_LEVELS * a.width);
+    sh.staged = 0;
   }
   team_sync<TEAM>();
   uint32_t f0 = 0, f1 = 1;
+  // undirected graphs walk the out-edge rows once per batch, so the settle
+  // step can stage the new batch's rows for the next expansion
+  const bool stage = BCGPU_STAGE && a.g.in_row_ptr == nullptr;
   for (;;) {
     const D split0 = sh.split;
     c0 = clock64();
@@ -756,7 +779,7 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
                                                    scanned);
     } else {
       expand_forward<D, TEAM, PACKED, WALK_BOTH>(a, out_rows(a.g), sl, sh, sl.S, f0, f1, s, t, split0, relax,
-                                                  scanned);
+                                                  scanned, sh.staged);
     }
     // DAG edges into the batch just expanded end here
     if (t == 0) sl.pend[sh.nlev - 1] = sh.pair_len;
@@ -861,7 +884,9 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
     const D split = sh.split;
     const uint32_t S0 = sh.S_len;
     uint32_t nset = 0, kept = 0;
+    bool staged_now = false;
     if (nl <= TEAM * NEAR_REGS) {
+      staged_now = stage;
       // the whole near queue fits in registers: one gather pass
       near_sc += nl;
       uint32_t uu[NEAR_REGS];
@@ -893,9 +918,25 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
         const uint32_t valid = j < nl;
         uint32_t take = valid && dd[r] < thr;
         if (valid && a.settle_in && !take) take = dd[r] < (D)(dm + dni[r]);
+        // the row bounds of a settling vertex load while the scan's barriers run
+        uint64_t rp0 = 0, rp1 = 0;
+        if (stage && take) {
+          rp0 = __ldg(&a.g.row_ptr[uu[r]]);
+          rp1 = __ldg(&a.g.row_ptr[uu[r] + 1]);
+        }
         uint32_t stot;
         const uint32_t sx = team_excl_scan<TEAM>(take, &stot, sh.scan);
-        if (take) sl.S[S0 + nset + sx] = uu[r];
+        if (take) {
+          const uint32_t idx = nset + sx;
+          sl.S[S0 + idx] = uu[r];
+          if (stage && idx < (uint32_t)TEAM) {
+            // the next expansion's first chunk: id, final distance, row
+            sh.vtx[idx] = uu[r];
+            sh.rs[idx] = rp0;
+            sh.dg[idx] = (uint32_t)(rp1 - rp0);
+            sh.dv[idx] = dd[r];
+          }
+        }
         if (valid && !take) sl.nearq[kept + (j - base) - sx] = uu[r];
         nset += stot;
         kept += min((uint32_t)TEAM, nl - base) - stot;
@@ -940,6 +981,7 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
     if (t == 0) {
       sh.near_len = kept;
       sh.S_len = S0 + nset;
+      sh.staged = staged_now ? min(nset, (uint32_t)TEAM) : 0u;
       sh.nlev += 1;
       sl.ends[sh.nlev] = S0 + nset;
       if (phases + refills > a.phase_cap) sh.stop = 1;
