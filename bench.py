@@ -150,6 +150,42 @@ def dist_env():
     return ws, rank, local
 
 
+class Replicas:
+    """Host-side coordination of N replicas (one process per GPU, launched by
+    torchrun).  Sources are independent, so there is no collective on the
+    data path: a barrier brackets each timed region and the slowest rank's
+    time is the job's time.  `dist` is torch.distributed after
+    init_process_group (nccl on GPUs, gloo in the CPU tests) or None."""
+
+    def __init__(self, dist=None, device=None):
+        self.dist = dist
+        self.device = device
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max_over_ranks(self, x: float) -> float:
+        if self.dist is None:
+            return x
+        import torch
+
+        t = torch.tensor([x], device=self.device, dtype=torch.float64)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+
+def whole_job_gteps(ws: int, k: int, m: int, seconds: float) -> float:
+    """Units every rank processed (each replica runs all k sources) over the slowest rank's time."""
+    return ws * k * m / seconds / 1e9
+
+
+def emit(line: dict, rank: int):
+    """Only rank 0 prints the JSON line."""
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def cpu_baseline(g, sources, seconds_target=15.0, max_sample=4096):
     """Time the CPU oracle (as it stands) on a bounded prefix of the source list."""
     import oracle
@@ -439,11 +475,9 @@ def main():
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
     dev = torch.device("cuda", local)
+    ranks = Replicas(dist, dev)
+    barrier = ranks.barrier
     if args.max_slots:
         bc.bc_set_config(max_slots=args.max_slots)
     G = bc.Graph(g)
@@ -499,12 +533,8 @@ def main():
     clk = clocks.stop()
     total_ms = t_start.elapsed_time(t_end)
     launch_ms = [a.elapsed_time(b) for a, b in ev]
-    ms_step = total_ms / args.steps
-    if dist is not None:
-        tt = torch.tensor([ms_step], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_step = float(tt.item())
-    value = ws * k * m / (ms_step * 1e-3) / 1e9
+    ms_step = ranks.max_over_ranks(total_ms / args.steps)
+    value = whole_job_gteps(ws, k, m, ms_step * 1e-3)
 
     # end to end through the public synchronous call: host sources in, host BC out
     host_out = np.empty(g.n, np.float64)
@@ -516,11 +546,7 @@ def main():
         dt = time.perf_counter() - t0
         if i > 0:
             e2e_times.append(dt)
-    e2e_s = statistics.mean(e2e_times)
-    if dist is not None:
-        tt = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = ranks.max_over_ranks(statistics.mean(e2e_times))
 
     # roofline of the dominant kernel (the batched kernel is > 99% of a step)
     rn, re_ = reach_model(g, sources)
@@ -542,7 +568,7 @@ def main():
                    "autotune": {"probe_sources": probe, "seconds": round(tune_s, 2)},
                    "launch": "bc_compute_async per step" if args.no_graph else "CUDA graph (bc_step_launch)",
                    "relabeled_by_degree": bool(G.info().relabeled), "dist_bits": int(G.info().dist_bits)},
-        "e2e": {"value": ws * k * m / e2e_s / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": 4 * k,
+        "e2e": {"value": whole_job_gteps(ws, k, m, e2e_s), "unit": "GTEPS", "h2d_bytes_per_step": 4 * k,
                 "d2h_bytes_per_step": 8 * g.n},
         "gpu_launches": 3 * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -566,8 +592,7 @@ def main():
         line["plain"] = {"value": len(sub) * m / dt / 1e9, "unit": "GTEPS", "sources": len(sub)}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g, sources)
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    emit(line, rank)
     if step_h is not None:
         bc.bc_step_destroy(step_h)
     G.close()

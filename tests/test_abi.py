@@ -41,7 +41,24 @@ def test_config_roundtrip_without_gpu(built):
     with pytest.raises(bc.BCError) as ei:
         bc.bc_set_config(team_threads=48)
     assert ei.value.code == bc.BC_ERR_INVALID
+    for bad in (dict(algorithm=3), dict(settle_in=3), dict(mem_fraction=0.99),
+                dict(warp_degree=64, team_degree=32), dict(mode=2)):
+        with pytest.raises(bc.BCError):
+            bc.bc_set_config(**bad)
+        assert bc.bc_get_config().team_threads == c.team_threads  # a refused config changes nothing
+    bc.bc_set_config(team_threads=1024, algorithm=bc.BC_ALGO_DELTA, hot_vertices=65536)
+    got = bc.bc_get_config()
+    assert (got.team_threads, got.algorithm, got.hot_vertices) == (1024, bc.BC_ALGO_DELTA, 65536)
     bc.bc_set_config(c)
+    assert bc.bc_get_config().algorithm == c.algorithm
+
+
+def test_step_and_request_calls_reject_null_handles_without_gpu(built):
+    for call in (lambda: bc.bc_step_launch(None, 0), lambda: bc.bc_step_sync(None, 0),
+                 lambda: bc.bc_step_destroy(None), lambda: bc.bc_step_create(None, 0, 0, 1.0, 0)):
+        with pytest.raises(bc.BCError) as ei:
+            call()
+        assert ei.value.code == bc.BC_ERR_INVALID
 
 
 def test_invalid_csr_rejected_before_any_device_call(built):
