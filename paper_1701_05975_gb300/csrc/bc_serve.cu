@@ -49,7 +49,15 @@ struct Request {
   int stream_idx = -1;
 };
 
-constexpr int kStreams = 8;
+// Requests on the device at once (one stream each), and the number of
+// waiting requests the resident threads are shared between.
+#ifndef BCGPU_SERVE_STREAMS
+#define BCGPU_SERVE_STREAMS 8
+#endif
+#ifndef BCGPU_SERVE_SHARE
+#define BCGPU_SERVE_SHARE 4
+#endif
+constexpr int kStreams = BCGPU_SERVE_STREAMS;
 constexpr size_t kMaxPending = 1 << 20;
 
 struct Server {
@@ -120,7 +128,7 @@ struct Server {
       return true;
     }
     const uint64_t waiting = running.size() + pending.size();
-    const uint64_t share = std::max<uint64_t>(thread_cap / std::max<uint64_t>(1, std::min<uint64_t>(waiting, 4)), p.team);
+    const uint64_t share = std::max<uint64_t>(thread_cap / std::max<uint64_t>(1, std::min<uint64_t>(waiting, BCGPU_SERVE_SHARE)), p.team);
     const uint64_t free_threads = thread_cap > threads_used ? thread_cap - threads_used : 0;
     uint64_t slots = std::min<uint64_t>({(uint64_t)std::max<size_t>(r->sources.size(), 1), p.max_slots,
                                          std::min(share, free_threads) / p.team});
