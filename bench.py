@@ -18,9 +18,11 @@ import hashlib
 import json
 import os
 import re
+import shutil
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -99,14 +101,16 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, keep_path=None):
+        """Samples go to a temporary file; `keep_path` (optional) keeps the raw CSV."""
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.keep_path = keep_path
+        fd, self.path = tempfile.mkstemp(prefix=f"clocks_rank{gpu_index}_", suffix=".csv")
+        os.close(fd)
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
@@ -116,6 +120,8 @@ class ClockSampler:
 
     def stop(self):
         if self.proc is None:
+            if os.path.exists(self.path):
+                os.unlink(self.path)
             return None
         self.proc.terminate()
         try:
@@ -137,6 +143,10 @@ class ClockSampler:
             for nm, val in zip(names, parts[5:9]):
                 if val.lower() == "active":
                     reasons.add(nm)
+        if self.keep_path:
+            os.makedirs(os.path.dirname(os.path.abspath(self.keep_path)), exist_ok=True)
+            shutil.copyfile(self.path, self.keep_path)
+        os.unlink(self.path)
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
@@ -439,6 +449,8 @@ def main():
     ap.add_argument("--sources", type=int, default=0,
                     help="use only the first K sources of the workload (small profiling cases); 0 = all")
     ap.add_argument("--max-slots", type=int, default=0, help="cap on sources in flight (0 = automatic)")
+    ap.add_argument("--clocks-csv", default="", help="also keep the raw nvidia-smi clock samples at this path "
+                    "({rank} is replaced by the rank)")
     ap.add_argument("--no-graph", action="store_true", help="enqueue each step with bc_compute_async instead of "
                     "replaying a captured step graph")
     args = ap.parse_args()
@@ -515,7 +527,7 @@ def main():
     st = G.stats()
     barrier()
     torch.cuda.synchronize(dev)
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(local, args.clocks_csv.replace("{rank}", str(rank)) if args.clocks_csv else None)
     clocks.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     with torch.cuda.stream(stream):
