@@ -55,7 +55,10 @@ __host__ __device__ constexpr int unroll_of() {
   return TEAM >= 1024 ? 6 : UNROLL;
 }
 constexpr int NEAR_REGS = 4;          // near-queue entries per thread kept in registers
-constexpr uint64_t FAR_LEVELS = 16;   // the second far level starts FAR_LEVELS split widths out
+#ifndef BCGPU_FAR_LEVELS
+#define BCGPU_FAR_LEVELS 16
+#endif
+constexpr uint64_t FAR_LEVELS = BCGPU_FAR_LEVELS;   // the second far level starts FAR_LEVELS split widths out
 
 template <typename D>
 __device__ __forceinline__ D dinf() {
