@@ -449,6 +449,8 @@ def main():
     ap.add_argument("--sources", type=int, default=0,
                     help="use only the first K sources of the workload (small profiling cases); 0 = all")
     ap.add_argument("--max-slots", type=int, default=0, help="cap on sources in flight (0 = automatic)")
+    ap.add_argument("--team", type=int, default=0, help="threads per source (0 = automatic / autotuned)")
+    ap.add_argument("--width", type=int, default=0, help="near/far split width (0 = automatic / autotuned)")
     ap.add_argument("--clocks-csv", default="", help="also keep the raw nvidia-smi clock samples at this path "
                     "({rank} is replaced by the rank)")
     ap.add_argument("--no-graph", action="store_true", help="enqueue each step with bc_compute_async instead of "
@@ -492,6 +494,10 @@ def main():
     barrier = ranks.barrier
     if args.max_slots:
         bc.bc_set_config(max_slots=args.max_slots)
+    if args.team:
+        bc.bc_set_config(team_threads=args.team)
+    if args.width:
+        bc.bc_set_config(bucket_width=args.width)
     G = bc.Graph(g)
     probe = args.autotune if args.autotune >= 0 else min(len(sources), 2048)
     tune_s = 0.0
@@ -574,7 +580,8 @@ def main():
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": desc, "n": g.n, "m": m, "nnz": g.nnz, "sources": k, "scale": scale,
-                   "l2": "inputs larger than L2 (CSR 251 MB + per-source slabs)",
+                   "l2": "inputs larger than L2: graph %.0f MB + %d per-source slabs of %.1f MB"
+                         % (G.info().device_bytes / 1e6, int(st.slots), G.info().slab_bytes / 1e6),
                    "team_threads": int(st.team_threads), "slots": int(st.slots),
                    "bucket_width": int(st.bucket_width), "parallelism": f"replicas x{ws}",
                    "autotune": {"probe_sources": probe, "seconds": round(tune_s, 2)},
