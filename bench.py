@@ -46,7 +46,49 @@ WORKLOADS = {
     "grid1024": ("perturbed 1024x1024 4-neighbour grid, 5% edges removed, weights U[1,10000], 1024 sources",
                  gen.workload_grid1024),
     "er1k": ("Erdos-Renyi G(1024, 8192), weights U[1,100], all sources, scale 0.5", gen.workload_er1k),
+    "rmat20-edge": ("edge BC (and vertex BC) on R-MAT scale 20, edge factor 16, a=.57 b=.19 c=.19, symmetrised, "
+                    "weights U[1,255], 4096 uniform sources, scale 0.5 n/k", gen.workload_rmat20),
+    "rmat20-directed": ("directed R-MAT scale 20, edge factor 16, a=.57 b=.19 c=.19, weights U[1,255], "
+                        "4096 uniform sources, ordered pairs, scale n/k", gen.workload_rmat20_directed),
+    "grid1024-delta": ("perturbed 1024x1024 4-neighbour grid, 5% edges removed, weights U[1,10000], 1024 sources, "
+                       "delta-stepping schedule with DAG hop-depth levels", gen.workload_grid1024),
 }
+
+# per-workload options: edge output, directed graph, per-source schedule
+WORKLOAD_OPTS = {"rmat20-edge": {"edge": True}, "rmat20-directed": {"directed": True},
+                 "grid1024-delta": {"algorithm": 2}}
+
+
+def oracle_fn(opts):
+    """The oracle form for a workload: (callable(g, sources, scale) -> BC, threads it uses per call)."""
+    import oracle
+
+    if opts.get("directed"):
+        return oracle.bc_directed, 1
+    if opts.get("edge"):
+        return oracle.edge_bc, 1
+    return None, 0
+
+
+def run_oracle(g, sources, scale, opts, cores):
+    """The oracle as it stands over `sources`; single-threaded forms run one
+    source chunk per host core (ctypes releases the GIL during each call)."""
+    import oracle
+
+    fn, _ = oracle_fn(opts)
+    if fn is None:
+        return oracle.bc(g, sources, scale, nthreads=cores)
+    import concurrent.futures
+
+    chunks = [c for c in np.array_split(np.asarray(sources), cores) if len(c)]
+    with concurrent.futures.ThreadPoolExecutor(max_workers=len(chunks)) as ex:
+        parts = list(ex.map(lambda c: fn(g, c, scale), chunks))
+    return np.sum(parts, axis=0)
+
+
+def edge_units(g, opts):
+    """Edges per source for TEPS: undirected edges, or directed edges."""
+    return g.nnz if opts.get("directed") else g.m
 
 # Algorithmic bytes per unit (the three-pass byte model of the method):
 # per CSR entry of a reached vertex 64 B (relax 16 + sigma 24 + backward 24),
@@ -56,13 +98,23 @@ BYTES_PER_VERTEX = 80
 KERNEL_SRC = os.path.join(ROOT, "paper_1701_05975_gb300", "csrc", "bc_batched.cuh")
 
 
-def reach_model(g, sources):
-    """Per-source reached vertices and reached CSR entries (component sizes)."""
+def reach_model(g, sources, directed=False, sample=32):
+    """Per-source reached vertices and reached CSR entries (component sizes;
+    for directed graphs the mean out-reach of a sample of the sources)."""
     import scipy.sparse as sp
-    from scipy.sparse.csgraph import connected_components
+    from scipy.sparse.csgraph import breadth_first_order, connected_components
 
     rows = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.row_ptr).astype(np.int64))
     mat = sp.csr_matrix((np.ones(len(rows), np.int8), (rows, g.col.astype(np.int64))), shape=(g.n, g.n))
+    if directed:
+        deg = np.diff(g.row_ptr).astype(np.float64)
+        rn, re_ = [], []
+        for s in np.asarray(sources)[:: max(1, len(sources) // sample)][:sample]:
+            order = breadth_first_order(mat, int(s), directed=True, return_predecessors=False)
+            rn.append(len(order))
+            re_.append(deg[order].sum())
+        k = len(sources)
+        return np.full(k, np.mean(rn)), np.full(k, np.mean(re_))
     _, lab = connected_components(mat, directed=False)
     comp_n = np.bincount(lab)
     comp_e = np.bincount(lab, weights=np.diff(g.row_ptr).astype(np.float64))
@@ -196,56 +248,59 @@ def emit(line: dict, rank: int):
         print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(g, sources, seconds_target=15.0, max_sample=4096):
+def cpu_baseline(g, sources, opts=None, seconds_target=15.0, max_sample=4096):
     """Time the CPU oracle (as it stands) on a bounded prefix of the source list."""
-    import oracle
-
+    opts = opts or {}
     cores = os.cpu_count() or 1
-    m = g.m
+    m = edge_units(g, opts)
     # probe a small prefix to size the sample
     k = min(len(sources), max(cores, 8))
     t0 = time.perf_counter()
-    oracle.bc(g, sources[:k], 1.0, nthreads=cores)
+    run_oracle(g, sources[:k], 1.0, opts, cores)
     dt = time.perf_counter() - t0
     if dt < seconds_target / 4 and k < len(sources):
         k2 = int(min(len(sources), max_sample, k * max(1.0, (seconds_target / max(dt, 1e-3)) * 0.8)))
         if k2 > k:
             k = k2
             t0 = time.perf_counter()
-            oracle.bc(g, sources[:k], 1.0, nthreads=cores)
+            run_oracle(g, sources[:k], 1.0, opts, cores)
             dt = time.perf_counter() - t0
     return {"value": k * m / dt / 1e9, "unit": "GTEPS", "cores": cores, "kind": "oracle",
             "sample": f"first {k} of {len(sources)} sources of the same workload, {dt:.2f} s, "
-                      f"{cores} POSIX threads"}
+                      f"{cores} host threads"}
 
 
-def run_reference(args, g, sources, scale, desc):
+def metric_name(opts):
+    return ("weighted-BC GTEPS (sources x directed edges / s)" if opts.get("directed")
+            else "weighted-BC GTEPS (sources x undirected edges / s)")
+
+
+def run_reference(args, g, sources, scale, desc, opts=None):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    import oracle
-
+    opts = opts or {}
     cores = os.cpu_count() or 1
-    m = g.m
+    m = edge_units(g, opts)
     # bounded sample per step: sized so the whole run stays within minutes
     k = min(len(sources), max(cores, 16))
     t0 = time.perf_counter()
-    oracle.bc(g, sources[:k], scale, nthreads=cores)
+    run_oracle(g, sources[:k], scale, opts, cores)
     probe = time.perf_counter() - t0
     budget_per_step = 150.0 / max(args.steps + args.warmup, 1)
     if probe < budget_per_step / 2:
         k = int(min(len(sources), k * max(1.0, 0.8 * budget_per_step / max(probe, 1e-3))))
     for _ in range(args.warmup):
-        oracle.bc(g, sources[:k], scale, nthreads=cores)
+        run_oracle(g, sources[:k], scale, opts, cores)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.bc(g, sources[:k], scale, nthreads=cores)
+        run_oracle(g, sources[:k], scale, opts, cores)
         times.append(time.perf_counter() - t0)
     t = max(statistics.mean(times), 1e-9)
     value = k * m / t / 1e9
     line = {
-        "impl": "reference", "metric": "weighted-BC GTEPS (sources x undirected edges / s)", "value": value,
+        "impl": "reference", "metric": metric_name(opts), "value": value,
         "unit": "GTEPS", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
@@ -467,15 +522,17 @@ def main():
         else:
             run_serving(args, desc)
         return
+    opts = WORKLOAD_OPTS.get(args.workload, {})
     g, sources, scale = maker()
     if args.sources:
         scale = scale * len(sources) / min(args.sources, len(sources))
         sources = sources[: args.sources]
-    m = g.m
+    m = edge_units(g, opts)
+    edge = bool(opts.get("edge"))
 
     ws, rank, local = dist_env()
     if args.impl == "reference":
-        run_reference(args, g, sources, scale, desc)
+        run_reference(args, g, sources, scale, desc, opts)
         return
 
     import torch
@@ -498,7 +555,9 @@ def main():
         bc.bc_set_config(team_threads=args.team)
     if args.width:
         bc.bc_set_config(bucket_width=args.width)
-    G = bc.Graph(g)
+    if opts.get("algorithm"):
+        bc.bc_set_config(algorithm=opts["algorithm"])
+    G = bc.Graph(g, flags=bc.BC_DIRECTED if opts.get("directed") else 0)
     probe = args.autotune if args.autotune >= 0 else min(len(sources), 2048)
     tune_s = 0.0
     if probe:
@@ -508,15 +567,21 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     d_src = torch.from_numpy(sources.astype(np.int32)).to(dev)
     d_out = torch.empty(g.n, dtype=torch.float64, device=dev)
+    d_ebc = torch.empty(g.nnz, dtype=torch.float64, device=dev) if edge else None
     k = len(sources)
 
     # a step is one batched run over all sources, captured once as a CUDA
     # graph (bc_step_create) and replayed; --no-graph enqueues it call by call
-    step_h = None if args.no_graph else bc.bc_step_create(G.handle, d_src.data_ptr(), k, scale, d_out.data_ptr())
+    # (edge output always does)
+    use_graph = not args.no_graph and not edge
+    step_h = bc.bc_step_create(G.handle, d_src.data_ptr(), k, scale, d_out.data_ptr()) if use_graph else None
 
     def step():
         if step_h is not None:
             bc.bc_step_launch(step_h, stream.cuda_stream)
+        elif edge:
+            bc.bc_edge_compute_async(G.handle, d_src.data_ptr(), k, scale, d_ebc.data_ptr(), d_out.data_ptr(),
+                                     stream.cuda_stream)
         else:
             bc.bc_compute_async(G.handle, d_src.data_ptr(), k, scale, d_out.data_ptr(), stream.cuda_stream)
 
@@ -556,18 +621,22 @@ def main():
 
     # end to end through the public synchronous call: host sources in, host BC out
     host_out = np.empty(g.n, np.float64)
+    host_ebc = np.empty(g.nnz, np.float64) if edge else None
     e2e_times = []
     for i in range(max(1, min(args.steps, 3)) + 1):
         barrier()
         t0 = time.perf_counter()
-        bc.bc_compute(G.handle, sources, scale, host_out)
+        if edge:
+            bc.bc_edge_compute(G.handle, sources, scale, host_ebc, host_out)
+        else:
+            bc.bc_compute(G.handle, sources, scale, host_out)
         dt = time.perf_counter() - t0
         if i > 0:
             e2e_times.append(dt)
     e2e_s = ranks.max_over_ranks(statistics.mean(e2e_times))
 
     # roofline of the dominant kernel (the batched kernel is > 99% of a step)
-    rn, re_ = reach_model(g, sources)
+    rn, re_ = reach_model(g, sources, directed=bool(opts.get("directed")))
     alg_bytes = float(BYTES_PER_ENTRY * re_.sum() + BYTES_PER_VERTEX * rn.sum())
     launch_avg_s = statistics.mean(launch_ms) * 1e-3
     achieved = alg_bytes / launch_avg_s / 1e9
@@ -575,7 +644,7 @@ def main():
     traffic = load_traffic(args.workload)
 
     line = {
-        "metric": "weighted-BC GTEPS (sources x undirected edges / s)",
+        "metric": metric_name(opts),
         "value": value, "unit": "GTEPS", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
@@ -585,11 +654,14 @@ def main():
                    "team_threads": int(st.team_threads), "slots": int(st.slots),
                    "bucket_width": int(st.bucket_width), "parallelism": f"replicas x{ws}",
                    "autotune": {"probe_sources": probe, "seconds": round(tune_s, 2)},
-                   "launch": "bc_compute_async per step" if args.no_graph else "CUDA graph (bc_step_launch)",
+                   "launch": "CUDA graph (bc_step_launch)" if use_graph else (
+                       "bc_edge_compute_async per step" if edge else "bc_compute_async per step"),
+                   "algorithm": "delta-stepping" if int(st.algorithm) == 2 else "strict",
                    "relabeled_by_degree": bool(G.info().relabeled), "dist_bits": int(G.info().dist_bits)},
         "e2e": {"value": whole_job_gteps(ws, k, m, e2e_s), "unit": "GTEPS", "h2d_bytes_per_step": 4 * k,
-                "d2h_bytes_per_step": 8 * g.n},
-        "gpu_launches": 3 * args.steps,
+                "d2h_bytes_per_step": 8 * g.n + (8 * g.nnz if edge else 0)},
+        # per step: source check, the batched kernel, then one scale pass per output when scale != 1
+        "gpu_launches": (2 + (scale != 1.0) * (2 if edge else 1)) * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                      "alg_bytes_per_launch": alg_bytes, "kernel": "bc_batched_kernel"},
@@ -598,7 +670,7 @@ def main():
                       "refills_per_source": st.refills / max(st.sources, 1),
                       "reached_per_source": st.reached / max(st.sources, 1)},
     }
-    if args.plain_sample and rank == 0:
+    if args.plain_sample and rank == 0 and not edge and not opts.get("directed"):
         sub = sources[: args.plain_sample]
         c0 = bc.bc_get_config()
         bc.bc_set_config(mode=bc.BC_MODE_PLAIN)
@@ -610,7 +682,7 @@ def main():
         bc.bc_set_config(c0)
         line["plain"] = {"value": len(sub) * m / dt / 1e9, "unit": "GTEPS", "sources": len(sub)}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(g, sources)
+        line["cpu_baseline"] = cpu_baseline(g, sources, opts)
     emit(line, rank)
     if step_h is not None:
         bc.bc_step_destroy(step_h)

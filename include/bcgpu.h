@@ -180,6 +180,13 @@ int bc_sync_status(bc_graph_t g, void *stream);
 int bc_edge_compute(bc_graph_t g, const uint32_t *sources, uint32_t k, double scale, double *out_ebc,
                     double *out_bc);
 
+/* Edge BC with DEVICE buffers on the caller's stream (the bc_compute_async
+ * form of bc_edge_compute): d_sources[k], d_out_ebc[nnz] (caller's entry ids)
+ * and d_out_bc[n] are device arrays the caller owns; both outputs are
+ * overwritten.  Status through bc_sync_status. */
+int bc_edge_compute_async(bc_graph_t g, const uint32_t *d_sources, uint32_t k, double scale, double *d_out_ebc,
+                          double *d_out_bc, void *stream);
+
 /*
  * The paper's own thread mappings, for comparison (Sec. 3.1-3.4, Fig. 2-5):
  * one source at a time over the whole GPU; each phase expands the frontier

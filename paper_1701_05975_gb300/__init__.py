@@ -102,6 +102,7 @@ _SIGNATURES = {
     "bc_autotune": [_vp, _vp, _u32],
     "bc_compute_noalloc": [_vp, _vp, _vp, _u32, _u64, _vp, _u32, _f64, _vp, _vp, _vp],
     "bc_compute_paper_variant": [_vp, _vp, _u32, _f64, _vp, _int, _int],
+    "bc_edge_compute_async": [_vp, _vp, _u32, _f64, _vp, _vp, _vp],
     "bc_step_create": [_vp, _vp, _u32, _f64, _vp, ctypes.POINTER(_vp)],
     "bc_step_launch": [_vp, _vp],
     "bc_step_sync": [_vp, _vp],
@@ -199,6 +200,12 @@ def bc_compute_paper_variant(h, sources, scale: float, out_bc: np.ndarray, node_
 
 def bc_sync_status(h, stream_ptr: int):
     _check(lib().bc_sync_status(h, ctypes.c_void_p(stream_ptr)))
+
+
+def bc_edge_compute_async(h, d_sources_ptr: int, k: int, scale: float, d_ebc_ptr: int, d_bc_ptr: int,
+                          stream_ptr: int):
+    _check(lib().bc_edge_compute_async(h, ctypes.c_void_p(d_sources_ptr), k, scale, ctypes.c_void_p(d_ebc_ptr),
+                                       ctypes.c_void_p(d_bc_ptr), ctypes.c_void_p(stream_ptr)))
 
 
 def bc_step_create(h, d_sources_ptr: int, k: int, scale: float, d_out_ptr: int):

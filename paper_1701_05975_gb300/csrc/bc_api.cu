@@ -92,6 +92,8 @@ SlabLayout make_layout(uint32_t n, int dist_bits) {
   off += align256((uint64_t)L.pair_cap * 8);
   L.off_pc = off;
   off += align256((uint64_t)n * 4);
+  L.off_pair_e = off;
+  off += align256((uint64_t)L.pair_cap * 4);
   L.stride = off;
   return L;
 }
@@ -158,6 +160,8 @@ struct bc_graph {
   uint32_t* o2n = nullptr;  // device maps (relabeled graphs only)
   uint32_t* n2o = nullptr;
   uint32_t* e2o = nullptr;
+  uint32_t* esm = nullptr;  // edge output: walked entry -> caller's output entry (built on first use)
+  int esm_state = 0;        // 0 not built, 1 ready, 2 unavailable (an entry without a twin)
   std::vector<uint32_t> h_o2n;  // host copy of old -> new
   uint64_t device_bytes = 0;
   std::string fingerprint;
@@ -342,6 +346,99 @@ void ws_release(bc_graph* g, Workspace* w, cudaStream_t st) {
   w->busy = false;
 }
 
+// Edge output over the DAG edge list needs, for every entry the forward pass
+// walks (out-entries of an undirected graph, in-entries of a directed one),
+// the caller's index of the entry that carries its share: the twin u -> v of
+// the walked entry v -> u, or the out-entry u -> v of the in-entry.  Built on
+// the host from the device CSR on the first edge-output call; a graph whose
+// undirected entries lack twins keeps the per-entry backward scan.
+int ensure_edge_map(bc_graph* g) {
+  {
+    std::lock_guard<std::mutex> lk(g->mu);
+    if (g->esm_state) return BC_OK;
+  }
+  const uint32_t n = g->n;
+  const uint64_t nnz = g->nnz;
+  std::vector<uint64_t> rp((size_t)n + 1);
+  std::vector<uint32_t> col(nnz), wt(nnz), e2o;
+  CK(cudaMemcpy(rp.data(), g->row_ptr, ((size_t)n + 1) * 8, cudaMemcpyDeviceToHost));
+  if (g->adjp) {
+    std::vector<uint32_t> p(nnz);
+    if (nnz) CK(cudaMemcpy(p.data(), g->adjp, nnz * 4, cudaMemcpyDeviceToHost));
+    const uint32_t mask = (g->col_bits >= 32) ? 0xffffffffu : ((1u << g->col_bits) - 1u);
+    for (uint64_t e = 0; e < nnz; ++e) {
+      col[e] = p[e] & mask;
+      wt[e] = p[e] >> g->col_bits;
+    }
+  } else {
+    std::vector<uint2> p(nnz);
+    if (nnz) CK(cudaMemcpy(p.data(), g->adj, nnz * 8, cudaMemcpyDeviceToHost));
+    for (uint64_t e = 0; e < nnz; ++e) {
+      col[e] = p[e].x;
+      wt[e] = p[e].y;
+    }
+  }
+  if (g->e2o) {
+    e2o.resize(nnz);
+    if (nnz) CK(cudaMemcpy(e2o.data(), g->e2o, nnz * 4, cudaMemcpyDeviceToHost));
+  }
+  auto out_id = [&](uint64_t e) { return g->e2o ? e2o[e] : (uint32_t)e; };
+  std::vector<uint32_t> map(std::max<uint64_t>(nnz, 1), 0);
+  bool ok = true;
+  if (g->directed) {
+    // in-entry order of the transpose built at creation: rows by target,
+    // within a row by source (the out-CSR's row order)
+    std::vector<uint64_t> fill((size_t)n + 1, 0);
+    for (uint64_t e = 0; e < nnz; ++e) ++fill[(size_t)col[e] + 1];
+    for (uint32_t v = 0; v < n; ++v) fill[v + 1] += fill[v];
+    for (uint32_t v = 0; v < n; ++v)
+      for (uint64_t e = rp[v]; e < rp[v + 1]; ++e) map[fill[col[e]]++] = out_id(e);
+  } else {
+    // each row sorted by (neighbour, weight, entry); the k-th entry v -> u of
+    // weight w pairs with the k-th entry u -> v of weight w
+    std::vector<uint32_t> perm(nnz);
+    for (uint64_t e = 0; e < nnz; ++e) perm[e] = (uint32_t)e;
+    auto less = [&](uint32_t x, uint32_t y) {
+      return col[x] != col[y] ? col[x] < col[y] : (wt[x] != wt[y] ? wt[x] < wt[y] : x < y);
+    };
+    for (uint32_t v = 0; v < n; ++v) std::sort(perm.begin() + rp[v], perm.begin() + rp[v + 1], less);
+    for (uint32_t a = 0; a < n && ok; ++a) {
+      uint64_t group = rp[a];
+      for (uint64_t i = rp[a]; i < rp[a + 1]; ++i) {
+        const uint32_t e = perm[i];
+        if (i > rp[a] && (col[perm[i - 1]] != col[e] || wt[perm[i - 1]] != wt[e])) group = i;
+        const uint64_t k = i - group;
+        const uint32_t b = col[e], w = wt[e];
+        auto first = std::lower_bound(perm.begin() + rp[b], perm.begin() + rp[b + 1], 0u,
+                                      [&](uint32_t x, uint32_t) { return col[x] != a ? col[x] < a : wt[x] < w; });
+        const uint64_t pos = (uint64_t)(first - perm.begin()) + k;
+        if (pos >= rp[b + 1] || col[perm[pos]] != a || wt[perm[pos]] != w) {
+          ok = false;
+          break;
+        }
+        map[e] = out_id(perm[pos]);
+      }
+    }
+  }
+  uint32_t* d_map = nullptr;
+  if (ok) {
+    CK(cudaMalloc(&d_map, std::max<uint64_t>(nnz, 1) * 4));
+    cudaError_t e = nnz ? cudaMemcpy(d_map, map.data(), nnz * 4, cudaMemcpyHostToDevice) : cudaSuccess;
+    if (e != cudaSuccess) {
+      cudaFree(d_map);
+      return cuda_fail(e, "edge map upload");
+    }
+  }
+  std::lock_guard<std::mutex> lk(g->mu);
+  if (g->esm_state) {  // built concurrently by another thread
+    cudaFree(d_map);
+    return BC_OK;
+  }
+  g->esm = d_map;
+  g->esm_state = ok ? 1 : 2;
+  return BC_OK;
+}
+
 BatchArgs make_args(bc_graph* g, Workspace* w, const RunCfg& r, const uint32_t* d_src, uint32_t k, double* d_bc,
                     double* d_ebc, uint32_t slots, uint32_t flags) {
   BatchArgs a{};
@@ -364,6 +461,7 @@ BatchArgs make_args(bc_graph* g, Workspace* w, const RunCfg& r, const uint32_t* 
   a.warp_deg = r.warp_deg;
   a.team_deg = r.team_deg;
   a.algo = r.algo;
+  a.esm = (d_ebc && g->esm_state == 1) ? g->esm : nullptr;
   // the highest-degree vertices after relabeling: 128 KiB of 32-bit distance
   // words per source (the whole L2 holds this prefix for ~1000 sources)
   a.hot_n = r.hot_n;
@@ -430,6 +528,8 @@ int compute_sync(bc_graph* g, const uint32_t* sources, uint32_t k, double scale,
                  const RunCfg& r) {
   for (uint32_t i = 0; i < k; ++i)
     if (sources[i] >= g->n) return fail(BC_ERR_INVALID, "source %u out of range (n = %u)", sources[i], g->n);
+  if (out_ebc)
+    if (int rc = ensure_edge_map(g)) return rc;
   cudaStream_t st = g->stream;
   uint32_t slots = 0;
   int rc = plan_slots(g, r, k, &slots);
@@ -846,6 +946,7 @@ int bc_graph_destroy(bc_graph_t g) {
   cudaFree(g->o2n);
   cudaFree(g->n2o);
   cudaFree(g->e2o);
+  cudaFree(g->esm);
   cudaFree(g->in_row_ptr);
   cudaFree(g->in_adj);
   cudaFree(g->in_adjp);
@@ -879,21 +980,28 @@ int bc_compute(bc_graph_t g, const uint32_t* sources, uint32_t k, double scale, 
   return compute_sync(g, sources, k, scale, out_bc, nullptr, r);
 }
 
-int bc_compute_async(bc_graph_t g, const uint32_t* d_sources, uint32_t k, double scale, double* d_out_bc,
-                     void* stream) {
+}  // extern "C"
+
+namespace {
+
+// Shared body of the async entry points: device sources in, device outputs.
+int compute_async(bc_graph* g, const uint32_t* d_sources, uint32_t k, double scale, double* d_out_bc,
+                  double* d_out_ebc, void* stream) {
   if (int rc = check_graph(g)) return rc;
   if (!d_out_bc) return fail(BC_ERR_INVALID, "null d_out_bc");
   if (k && !d_sources) return fail(BC_ERR_INVALID, "null d_sources");
   CK(cudaSetDevice(g->device));
   RunCfg r = resolve(g);
-  if (r.mode != BC_MODE_BATCHED) return fail(BC_ERR_INVALID, "bc_compute_async runs the batched mode only");
+  if (r.mode != BC_MODE_BATCHED) return fail(BC_ERR_INVALID, "the async entry points run the batched mode only");
+  if (d_out_ebc)
+    if (int rc = ensure_edge_map(g)) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   uint32_t slots = 0;
   int rc = plan_slots(g, r, k, &slots);
   if (rc) return rc;
   Workspace* w = nullptr;
   if ((rc = ws_acquire(g, slots, 0, st, &w))) return rc;
-  rc = enqueue_batched(g, w, r, d_sources, k, scale, d_out_bc, nullptr, slots, 0, st, true);
+  rc = enqueue_batched(g, w, r, d_sources, k, scale, d_out_bc, d_out_ebc, slots, 0, st, true);
   if (!rc) {
     cudaError_t e = cudaMemcpyAsync(w->host_ctl, w->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemcpyAsync(control)");
@@ -908,6 +1016,21 @@ int bc_compute_async(bc_graph_t g, const uint32_t* d_sources, uint32_t k, double
   }
   ws_release(g, w, st);
   return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bc_compute_async(bc_graph_t g, const uint32_t* d_sources, uint32_t k, double scale, double* d_out_bc,
+                     void* stream) {
+  return compute_async(g, d_sources, k, scale, d_out_bc, nullptr, stream);
+}
+
+int bc_edge_compute_async(bc_graph_t g, const uint32_t* d_sources, uint32_t k, double scale, double* d_out_ebc,
+                          double* d_out_bc, void* stream) {
+  if (!d_out_ebc) return fail(BC_ERR_INVALID, "null d_out_ebc");
+  return compute_async(g, d_sources, k, scale, d_out_bc, d_out_ebc, stream);
 }
 
 int bc_sync_status(bc_graph_t g, void* stream) {

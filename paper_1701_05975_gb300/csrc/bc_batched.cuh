@@ -375,6 +375,7 @@ struct Slab {
   uint2* pairs;     // DAG edges {predecessor u, vertex v}
   uint32_t pair_cap;
   uint32_t* pc;     // delta-stepping: round stamps, then predecessor counts (zero between sources)
+  uint32_t* pair_e; // edge output: the walked entry of each DAG edge, else nullptr
 };
 
 template <typename D>
@@ -393,6 +394,7 @@ __device__ __forceinline__ Slab<D> slab_at(const BatchArgs& a, uint32_t slot) {
   s.pairs = reinterpret_cast<uint2*>(base + a.lay.off_pairs);
   s.pair_cap = a.lay.pair_cap;
   s.pc = reinterpret_cast<uint32_t*>(base + a.lay.off_pc);
+  s.pair_e = (a.ebc && a.esm && a.lay.off_pair_e) ? reinterpret_cast<uint32_t*>(base + a.lay.off_pair_e) : nullptr;
   return s;
 }
 
@@ -447,7 +449,8 @@ enum : int { WALK_BOTH = 0, WALK_PULL = 1, WALK_RELAX = 2, WALK_DS = 3, WALK_COU
 
 template <typename D, int TEAM, int MODE>
 __device__ __forceinline__ void visit_entry(const Slab<D>& sl, TeamShared<D, TEAM>& sh, uint32_t i, uint2 ent, D du,
-                                            D split, unsigned long long& relax, uint32_t hot_n, uint64_t pol_last) {
+                                            D split, unsigned long long& relax, uint32_t hot_n, uint64_t pol_last,
+                                            uint64_t eidx) {
   (void)hot_n;
   (void)pol_last;
   const D INF = dinf<D>();
@@ -488,8 +491,12 @@ __device__ __forceinline__ void visit_entry(const Slab<D>& sl, TeamShared<D, TEA
     atomicAdd(&sh.acc[i], ldg_slab(&sl.sig[u]));
 #endif
     const uint32_t pos = atomicAdd(&sh.pair_len, 1u);
-    if (pos < sl.pair_cap) sl.pairs[pos] = make_uint2(u, sh.vtx[i]);
-    else sh.pair_over = 1;
+    if (pos < sl.pair_cap) {
+      sl.pairs[pos] = make_uint2(u, sh.vtx[i]);
+      if (sl.pair_e) sl.pair_e[pos] = (uint32_t)eidx;
+    } else {
+      sh.pair_over = 1;
+    }
   } else if (MODE != WALK_PULL) {
     const D nd = dvi + w;
     if (nd < du) {
@@ -536,7 +543,8 @@ __device__ __forceinline__ void walk_row(const BatchArgs& a, const Rows& rows, c
     for (int q = 0; q < UNR; ++q) dus[q] = (e0 + q * lanes < deg) ? gather_d(sl.d, ent[q].x, a.hot_n, pl) : INF;
 #pragma unroll
     for (int q = 0; q < UNR; ++q)
-      if (e0 + q * lanes < deg) visit_entry<D, TEAM, MODE>(sl, sh, i, ent[q], dus[q], split, relax, a.hot_n, pl);
+      if (e0 + q * lanes < deg)
+        visit_entry<D, TEAM, MODE>(sl, sh, i, ent[q], dus[q], split, relax, a.hot_n, pl, r0 + e0 + q * lanes);
   }
 }
 
@@ -630,7 +638,9 @@ __device__ void expand_forward(const BatchArgs& a, const Rows& rows, const Slab<
       for (int q = 0; q < UNR; ++q) dus[q] = (iv[q] != NONE) ? gather_d(sl.d, ent[q].x, a.hot_n, pl) : INF;
 #pragma unroll
       for (int q = 0; q < UNR; ++q)
-        if (iv[q] != NONE) visit_entry<D, TEAM, MODE>(sl, sh, iv[q], ent[q], dus[q], split, relax, a.hot_n, pl);
+        if (iv[q] != NONE)
+          visit_entry<D, TEAM, MODE>(sl, sh, iv[q], ent[q], dus[q], split, relax, a.hot_n, pl,
+                                     sh.rs[iv[q]] + (e0 + q * TEAM - sh.off[iv[q]]));
     }
     team_sync<TEAM>();
     if ((MODE == WALK_BOTH || MODE == WALK_PULL) && (uint32_t)t < cnt && sh.vtx[t] != s)
@@ -735,6 +745,41 @@ __device__ __forceinline__ void push_level_pairs(const uint2* pairs, double* bac
 #pragma unroll
     for (int q = 0; q < UNR; ++q)
       if (pr[q].x != NONE) atomicAdd(&bacc[pr[q].x], c[q]);
+  }
+}
+
+// The same step with edge output: the DAG edge u -> v also adds its share
+// sigma(u) * c(v) (u's sigma is still intact: u lies in an earlier level) to
+// the output entry esm[walked entry] (Sec. 1's edge BC, per CSR entry).
+template <int TEAM>
+__device__ __forceinline__ void push_level_pairs_edges(const uint2* pairs, const uint32_t* pair_e,
+                                                       const uint32_t* esm, double* bacc, const double* sig,
+                                                       double* ebc, uint32_t p0, uint32_t p1, int t) {
+  constexpr int UNR = 2;
+  for (uint32_t p = p0 + t; p < p1; p += TEAM * UNR) {
+    uint2 pr[UNR];
+    uint32_t pe[UNR];
+#pragma unroll
+    for (int q = 0; q < UNR; ++q) {
+      const bool ok = p + q * TEAM < p1;
+      pr[q] = ok ? __ldcg(&pairs[p + q * TEAM]) : make_uint2(NONE, 0);
+      pe[q] = ok ? __ldcg(&pair_e[p + q * TEAM]) : 0u;
+    }
+    double c[UNR], su[UNR];
+    uint32_t tg[UNR];
+#pragma unroll
+    for (int q = 0; q < UNR; ++q) {
+      const bool ok = pr[q].x != NONE;
+      c[q] = ok ? __ldcg(&sig[pr[q].y]) : 0.0;
+      su[q] = ok ? __ldcg(&sig[pr[q].x]) : 0.0;
+      tg[q] = ok ? __ldg(&esm[pe[q]]) : 0u;
+    }
+#pragma unroll
+    for (int q = 0; q < UNR; ++q)
+      if (pr[q].x != NONE) {
+        atomicAdd(&bacc[pr[q].x], c[q]);
+        atomicAdd(&ebc[tg[q]], su[q] * c[q]);
+      }
   }
 }
 
@@ -1012,13 +1057,17 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
   } else {
     const uint32_t nlev = sh.nlev;
     c0 = clock64();
-    if (!a.ebc && !sh.pair_over) {
+    if ((!a.ebc || sl.pair_e) && !sh.pair_over) {
       // Algorithm 3 over the recorded DAG edges: levels in reverse; finalize
       // the level's vertices, then push their coefficients to predecessors
       for (int lev = (int)nlev - 1; lev >= 1; --lev) {
         finalize_level<D, TEAM>(a, sl, ldcg(&sl.ends[lev]), ldcg(&sl.ends[lev + 1]), t);
         team_sync<TEAM>();
-        push_level_pairs<TEAM>(sl.pairs, sl.bacc, sl.sig, ldcg(&sl.pend[lev - 1]), ldcg(&sl.pend[lev]), t);
+        if (sl.pair_e)
+          push_level_pairs_edges<TEAM>(sl.pairs, sl.pair_e, a.esm, sl.bacc, sl.sig, a.ebc, ldcg(&sl.pend[lev - 1]),
+                                       ldcg(&sl.pend[lev]), t);
+        else
+          push_level_pairs<TEAM>(sl.pairs, sl.bacc, sl.sig, ldcg(&sl.pend[lev - 1]), ldcg(&sl.pend[lev]), t);
         team_sync<TEAM>();
       }
       if (t == 0) sl.bacc[s] = 0.0;  // the source collected shares it does not keep

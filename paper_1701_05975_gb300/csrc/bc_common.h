@@ -48,6 +48,7 @@ struct GraphDev {
 struct SlabLayout {
   uint64_t stride;
   uint64_t off_d, off_sig, off_S, off_ends, off_near, off_far, off_far2, off_acc, off_pend, off_pairs, off_pc;
+  uint64_t off_pair_e;  // entry walked by each DAG edge (edge output); 0 = not in this layout
   uint32_t pair_cap;
 };
 
@@ -95,6 +96,7 @@ struct BatchArgs {
   uint32_t* counter;  // [0]: next source index (zeroed before launch)
   double* bc;         // [n] raw sum of delta (scale applied afterwards)
   double* ebc;        // [nnz] raw per-entry shares, or nullptr
+  const uint32_t* esm; // edge output with the DAG edge list: walked entry -> output entry, or nullptr
   char* slabs;
   SlabLayout lay;
   uint32_t nslots;

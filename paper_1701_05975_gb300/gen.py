@@ -308,6 +308,14 @@ def workload_rmat20(k: int = 4096):
     return g, src, 0.5 * g.n / k
 
 
+def workload_rmat20_directed(k: int = 4096):
+    """Directed R-MAT scale 20 (every generated pair kept as a directed edge),
+    4096 uniform sources; ordered pairs, so the sampled scale is n / k."""
+    g = rmat_digraph(20, 16, 0.57, 0.19, 0.19, 1, 255, seed=0)
+    src = sample_sources(g.n, k, seed=0)
+    return g, src, g.n / k
+
+
 def workload_grid1024(k: int = 1024):
     g = grid_graph(1024, 1024, remove=104755, wmin=1, wmax=10000, seed=0)
     src = sample_sources(g.n, k, seed=0)

@@ -98,6 +98,9 @@ def test_edge_cases():
             with bc.Graph(g) as G:
                 assert_bc_close(G.compute(src, 0.5), oracle.bc(g, src, 0.5))
                 assert np.all(G.compute(np.zeros(0, np.uint32), 0.5) == 0)
+                # edge output: parallel entries and self-loops pair with their twins
+                ebc, _ = G.edge_compute(src, 0.5)
+                assert_bc_close(ebc, oracle.edge_bc(g, src, 0.5))
 
 
 def test_levels_are_legal_and_distances_exact_on_er1k():
@@ -166,6 +169,25 @@ def test_edge_bc_matches_oracle():
         ebc, vbc = G.edge_compute(src, 0.5)
     assert_bc_close(ebc, oracle.edge_bc(g, src, 0.5))
     assert_bc_close(vbc, oracle.bc(g, src, 0.5))
+
+
+def test_edge_bc_async_device_buffers():
+    torch = pytest.importorskip("torch")
+    for g, flags, ref in ((gen.er_graph(300, 1200, 1, 5, seed=12), 0, oracle.bc),
+                          (gen.rmat_digraph(12, 8, wmin=1, wmax=255, seed=7), bc.BC_DIRECTED, oracle.bc_directed)):
+        src = gen.sample_sources(g.n, 48, seed=5)
+        with bc.Graph(g, flags=flags | bc.BC_RELABEL_DEGREE) as G:
+            d_src = torch.from_numpy(src.astype(np.int32)).cuda()
+            d_ebc = torch.full((g.nnz,), 3.0, dtype=torch.float64, device="cuda")
+            d_bc = torch.full((g.n,), 3.0, dtype=torch.float64, device="cuda")
+            st = torch.cuda.Stream()
+            bc.bc_edge_compute_async(G.handle, d_src.data_ptr(), len(src), 0.5, d_ebc.data_ptr(), d_bc.data_ptr(),
+                                     st.cuda_stream)
+            bc.bc_sync_status(G.handle, st.cuda_stream)
+            assert_bc_close(d_ebc.cpu().numpy(), oracle.edge_bc(g, src, 0.5))
+            assert_bc_close(d_bc.cpu().numpy(), ref(g, src, 0.5))
+            with pytest.raises(bc.BCError):
+                bc.bc_edge_compute_async(G.handle, d_src.data_ptr(), len(src), 0.5, 0, d_bc.data_ptr(), st.cuda_stream)
 
 
 def test_errors_and_timeout_recovery():
@@ -239,6 +261,9 @@ def test_dag_edge_list_overflow_falls_back_to_entry_scan():
             assert_bc_close(G.compute(src, 0.5), oracle.bc(g, src, 0.5))
             st = G.stats()
             assert st.pair_overflows > 0
+            ebc, _ = G.edge_compute(src, 0.5)  # edge output falls back to the entry scan too
+            assert_bc_close(ebc, oracle.edge_bc(g, src, 0.5))
+            assert G.stats().pair_overflows > 0
             d, sg, _ = G.sssp_debug(0)
             d_ref, sg_ref, _ = oracle.sssp(g, 0)
             assert np.array_equal(d, d_ref) and np.array_equal(sg, sg_ref)
