@@ -79,6 +79,56 @@ def check_workload(g, sources, scale, parts, n_oracle, n_debug, tune=False):
         return full, stats
 
 
+def test_rmat20_directed_full_launch():
+    g, sources, scale = gen.workload_rmat20_directed()
+    with bc.Graph(g, flags=bc.BC_DIRECTED) as G:
+        G.autotune(sources[:2048])
+        full = run_step(G, g.n, sources, scale)
+        st = G.stats()
+        assert st.sources == len(sources) and st.pair_overflows == 0
+        total = np.zeros(g.n)
+        for chunk in np.array_split(sources, 4):
+            total += run_async(G, g.n, chunk, scale)
+        assert_close(full, total, rel=1e-11)
+        # sources with out-edges reach part of the graph; compare every output
+        outdeg = np.diff(g.row_ptr)
+        sample = np.array([int(s) for s in sources if outdeg[s] > 0][:6], np.uint32)
+        assert_close(run_async(G, g.n, sample, 1.0), oracle.bc_directed(g, sample, 1.0))
+        for s in sample[:2]:
+            d, sg, _ = G.sssp_debug(int(s))
+            d_ref, sg_ref, _ = oracle.sssp(g, int(s))
+            assert np.array_equal(d, d_ref) and np.array_equal(sg, sg_ref)
+
+
+def run_edge_async(G, g, sources, scale):
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda:0")
+    d_src = torch.from_numpy(np.ascontiguousarray(sources, dtype=np.uint32).view(np.int32)).to(dev)
+    d_ebc = torch.empty(g.nnz, dtype=torch.float64, device=dev)
+    d_bc = torch.empty(g.n, dtype=torch.float64, device=dev)
+    st = torch.cuda.Stream()
+    bc.bc_edge_compute_async(G.handle, d_src.data_ptr(), len(sources), scale, d_ebc.data_ptr(), d_bc.data_ptr(),
+                             st.cuda_stream)
+    bc.bc_sync_status(G.handle, st.cuda_stream)
+    return d_ebc.cpu().numpy(), d_bc.cpu().numpy()
+
+
+def test_rmat20_edge_full_launch():
+    g, sources, scale = gen.workload_rmat20()
+    with bc.Graph(g) as G:
+        G.autotune(sources[:2048])
+        ebc, vbc = run_edge_async(G, g, sources, scale)
+        st = G.stats()
+        assert st.sources == len(sources) and st.pair_overflows == 0  # the DAG-edge backward ran
+        assert_close(vbc, run_async(G, g.n, sources, scale), rel=1e-11)
+        parts = [run_edge_async(G, g, c, scale)[0] for c in np.array_split(sources, 2)]
+        assert_close(ebc, parts[0] + parts[1], rel=1e-11)
+        # a sample of sources: every entry's share against the oracle
+        deg = g.degrees()
+        sample = np.array([int(s) for s in sources if deg[s] > 0][:4], np.uint32)
+        assert_close(run_edge_async(G, g, sample, 1.0)[0], oracle.edge_bc(g, sample, 1.0))
+
+
 def test_rmat20_full_launch():
     g, sources, scale = gen.workload_rmat20()
     full, stats = check_workload(g, sources, scale, parts=4, n_oracle=6, n_debug=2, tune=True)
