@@ -97,7 +97,9 @@ typedef struct bc_config {
   uint32_t settle_in;     /* 1: settle by the strict OUT criterion (Eq. 2 + Eq. 4) OR the strict IN
                              criterion; 2: OUT only (the paper's criterion alone); 0 = automatic (1) */
   uint64_t bucket_width;  /* near/far split width, in distance units (>= 1) */
-  uint64_t phase_cap;     /* device cap on phases per source; hitting it returns BC_ERR_TIMEOUT */
+  uint64_t phase_cap;     /* device cap on phases + queue refills per source; hitting it returns BC_ERR_TIMEOUT.
+                             0 = automatic: 4n + 64, above what any valid input needs (phases <= n,
+                             refills <= 3n + 2) */
   double mem_fraction;    /* share of free device memory the slabs may take (0 < f <= 0.95) */
   uint32_t warp_degree;   /* forward expansion: rows with at least this many entries get one warp each */
   uint32_t team_degree;   /* ... and rows with at least this many entries the whole team (>= warp_degree) */

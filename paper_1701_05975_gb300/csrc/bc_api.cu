@@ -248,7 +248,10 @@ RunCfg resolve(const bc_graph* g) {
                            : (g->tuned.width ? g->tuned.width : std::max<uint64_t>(1, g->max_w / 4));
   uint32_t si = c.settle_in ? c.settle_in : (g->tuned.settle_in ? g->tuned.settle_in : 1u);
   r.settle_in = (si == 1u) ? 1u : 0u;
-  r.phase_cap = c.phase_cap ? c.phase_cap : 2ull * g->n + 64;
+  // phases <= n (each settles at least the smallest candidate), refills that
+  // move entries <= n per queue level, empty refills <= second-level refills + 2:
+  // phases + refills <= 4n + 2 (delta-stepping rounds + advances <= 3n)
+  r.phase_cap = c.phase_cap ? c.phase_cap : 4ull * g->n + 64;
   r.max_slots = c.max_slots ? c.max_slots : g->tuned.max_slots;
   r.mem_fraction = c.mem_fraction > 0 ? c.mem_fraction : 0.6;
   r.warp_deg = c.warp_degree ? c.warp_degree : (g->tuned.warp_deg ? g->tuned.warp_deg : 32u);

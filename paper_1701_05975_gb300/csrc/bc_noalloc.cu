@@ -214,7 +214,7 @@ extern "C" int bc_compute_noalloc(const uint64_t* d_row_ptr, const uint32_t* d_c
     a.nslots = (uint32_t)slots;
     a.width = cfg.bucket_width ? cfg.bucket_width : 64;
     a.settle_in = cfg.settle_in == 2 ? 0u : 1u;
-    a.phase_cap = cfg.phase_cap ? cfg.phase_cap : 2ull * n + 64;
+    a.phase_cap = cfg.phase_cap ? cfg.phase_cap : 4ull * n + 64;  // phases + refills <= 4n + 2
     a.err = &ctl->err;
     a.stats = ctl->stats;
     a.flags = 0;

@@ -190,6 +190,20 @@ def test_edge_bc_async_device_buffers():
                 bc.bc_edge_compute_async(G.handle, d_src.data_ptr(), len(src), 0.5, 0, d_bc.data_ptr(), st.cuda_stream)
 
 
+def test_default_cap_covers_tiny_split_widths():
+    # a split width far below the weights makes almost every vertex its own
+    # near-queue refill and second-level refill: phases + refills reach ~3n,
+    # above a 2n bound, and the default cap (4n + 64) must still not trip
+    g = gen.er_graph(2000, 8000, 1, 1 << 20, seed=77)
+    src = np.array([5], np.uint32)
+    for team in (128, 1024):
+        bc.bc_set_config(team_threads=team, bucket_width=1)
+        with bc.Graph(g) as G:
+            assert_bc_close(G.compute(src, 1.0), oracle.bc(g, src, 1.0))
+            st = G.stats()
+            assert st.phases + st.refills > 2 * g.n + 64, (st.phases, st.refills)
+
+
 def test_errors_and_timeout_recovery():
     g = gen.er_graph(500, 2000, 1, 30, seed=4)
     src = np.arange(50, dtype=np.uint32)
