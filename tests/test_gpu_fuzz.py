@@ -22,7 +22,7 @@ def default_config():
 
 
 def random_graph(rng):
-    kind = rng.choice(["small", "er", "ba", "rmat", "grid", "digraph", "rmatd"])
+    kind = rng.choice(["small", "er", "ba", "rmat", "grid", "digraph", "rmatd", "big"])
     wmax = int(rng.choice([1, 7, 300, 1 << 20]))
     seed = int(rng.integers(1 << 30))
     if kind == "small":
@@ -41,12 +41,16 @@ def random_graph(rng):
     if kind == "digraph":
         n = int(rng.integers(1, 120))
         return gen.random_small_digraph(n, float(rng.choice([0.02, 0.1, 0.3])), 1, wmax, rng), True
-    return gen.rmat_digraph(int(rng.integers(6, 11)), 8, wmin=1, wmax=wmax, seed=seed), True
+    if kind == "rmatd":
+        return gen.rmat_digraph(int(rng.integers(6, 11)), 8, wmin=1, wmax=wmax, seed=seed), True
+    # a larger graph: several chunks per batch and long queues
+    return gen.rmat_graph(13, 16, wmin=1, wmax=int(rng.choice([3, 255])), seed=seed), False
 
 
-def test_random_graphs_random_configurations():
-    rng = np.random.default_rng(20261203)
-    for it in range(120):
+@pytest.mark.parametrize("seed", [20261203, 7, 99])
+def test_random_graphs_random_configurations(seed):
+    rng = np.random.default_rng(seed)
+    for it in range(150):
         g, directed = random_graph(rng)
         cfg = dict(team_threads=int(rng.choice([32, 128, 256, 512, 1024])),
                    bucket_width=int(rng.choice([0, 1, 5, 100, 1 << 30])),
