@@ -106,3 +106,62 @@ def test_cancel_and_poll():
             bc.bc_request_poll(ids[0])  # forgotten after wait
         ref = G.compute(src, 1.0)
         assert_close(outs[0], ref)
+
+
+def test_randomised_stream_against_the_oracle():
+    """Random graphs (directed ones too), random source lists (empty, repeated),
+    random scales, a tight memory budget so requests queue, and cancellations:
+    every completed request equals the oracle, every cancelled one is reported."""
+    import oracle
+
+    rng = np.random.default_rng(11)
+    pool, flags = [], []
+    for i in range(6):
+        if i % 3 == 2:
+            pool.append(gen.random_small_digraph(int(rng.integers(20, 90)), 0.08, 1, 50, rng))
+            flags.append(bc.BC_DIRECTED)
+        else:
+            pool.append(gen.er_graph(int(rng.integers(200, 3000)), int(rng.integers(600, 9000)), 1,
+                                     int(rng.choice([5, 1000])), seed=int(rng.integers(1 << 30))))
+            flags.append(0)
+    graphs = [bc.Graph(g, flags=f) for g, f in zip(pool, flags)]
+    slab = max(G.info().slab_bytes for G in graphs)
+    free_b = __import__("torch").cuda.mem_get_info()[0]
+    # room for about forty slabs at a time: requests wait for each other
+    bc.bc_set_config(mem_fraction=min(0.5, max(1e-4, 40.0 * slab / free_b)))
+    reqs, outs, ids = [], [], []
+    bc.bc_serving_reset()
+    for i in range(60):
+        gi = int(rng.integers(len(pool)))
+        n = pool[gi].n
+        k = int(rng.integers(0, min(n, 96) + 1))
+        src = rng.choice(n, size=k, replace=bool(rng.integers(2))).astype(np.uint32)
+        scale = float(rng.choice([1.0, 0.5, 2.5]))
+        out = np.full(n, -7.0)
+        reqs.append((gi, src, scale))
+        outs.append(out)
+        ids.append(bc.bc_request_submit(graphs[gi].handle, src, scale, out))
+    cancelled = set()
+    for j in rng.choice(len(ids), size=8, replace=False):
+        try:
+            bc.bc_request_cancel(ids[j])
+            if bc.bc_request_poll(ids[j]) == bc.BC_REQ_CANCELLED:
+                cancelled.add(int(j))
+        except bc.BCError as e:
+            assert e.code == bc.BC_ERR_BUSY  # already running
+    for j, rid in enumerate(ids):
+        if j in cancelled:
+            with pytest.raises(bc.BCError) as ei:
+                bc.bc_request_wait(rid, 120000)
+            assert ei.value.code == bc.BC_ERR_CANCELLED
+        else:
+            bc.bc_request_wait(rid, 120000)
+    for j, ((gi, src, scale), out) in enumerate(zip(reqs, outs)):
+        if j in cancelled:
+            continue
+        ref = oracle.bc_directed if flags[gi] else oracle.bc
+        assert_close(out, ref(pool[gi], src, scale))
+    st = bc.bc_serving_stats_get()
+    assert st.completed == len(reqs) - len(cancelled) and st.failed == 0
+    for G in graphs:
+        G.close()
