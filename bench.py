@@ -107,12 +107,16 @@ def reach_model(g, sources, directed=False, sample=32):
     rows = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.row_ptr).astype(np.int64))
     mat = sp.csr_matrix((np.ones(len(rows), np.int8), (rows, g.col.astype(np.int64))), shape=(g.n, g.n))
     if directed:
+        # out-entries of the reached vertices carry the relaxation (16 B) and
+        # the backward pass (24 B), their in-entries the sigma pull (24 B):
+        # returned as 64-byte-equivalent entries
         deg = np.diff(g.row_ptr).astype(np.float64)
+        indeg = np.bincount(g.col.astype(np.int64), minlength=g.n).astype(np.float64)
         rn, re_ = [], []
         for s in np.asarray(sources)[:: max(1, len(sources) // sample)][:sample]:
             order = breadth_first_order(mat, int(s), directed=True, return_predecessors=False)
             rn.append(len(order))
-            re_.append(deg[order].sum())
+            re_.append((40.0 * deg[order].sum() + 24.0 * indeg[order].sum()) / BYTES_PER_ENTRY)
         k = len(sources)
         return np.full(k, np.mean(rn)), np.full(k, np.mean(re_))
     _, lab = connected_components(mat, directed=False)
