@@ -120,7 +120,8 @@ const char *bc_last_error(void);
 /*
  * Upload a graph (Sec. 3.1 CSR + weight array) to the current device.
  * row_ptr[n + 1], col_idx[nnz] and w[nnz] are HOST arrays; the library copies
- * them and the caller keeps ownership.  Validation: n >= 1, row_ptr[0] = 0,
+ * them and the caller keeps ownership.  Limits: 1 <= n <= 0xFFFFFFF0 and nnz < 2^32
+ * (checked before any array is read).  Validation: n >= 1, row_ptr[0] = 0,
  * non-decreasing, row_ptr[n] = nnz, col_idx < n, w >= 1; with
  * BC_UNDIRECTED_CHECK also the symmetry of the entries.  Precomputes
  * Delta_node(v) = min incident weight (Sec. 3.2, before Eq. 2).  Internal

@@ -53,6 +53,24 @@ def test_config_roundtrip_without_gpu(built):
     assert bc.bc_get_config().algorithm == c.algorithm
 
 
+def test_size_limits_rejected_before_reading_arrays(built):
+    import ctypes
+
+    import numpy as np
+    L = bc.lib(built)
+    h = ctypes.c_void_p()
+    # 2^32 CSR entries: rejected from row_ptr[n] alone (the entry arrays are never read)
+    rp = np.array([0, 1 << 32], np.uint64)
+    one = np.zeros(1, np.uint32)
+    rc = L.bc_graph_create(rp.ctypes.data, one.ctypes.data, one.ctypes.data, 1, 1 << 32, 0, ctypes.byref(h))
+    assert rc == bc.BC_ERR_INVALID and b"2^32" in L.bc_last_error()
+    # more vertices than ids below the reserved sentinels
+    rc = L.bc_graph_create(rp.ctypes.data, one.ctypes.data, one.ctypes.data, 0xFFFFFFF1, 0, 0, ctypes.byref(h))
+    assert rc == bc.BC_ERR_INVALID and b"n too large" in L.bc_last_error()
+    rc = L.bc_graph_create(rp.ctypes.data, one.ctypes.data, one.ctypes.data, 0, 0, 0, ctypes.byref(h))
+    assert rc == bc.BC_ERR_INVALID
+
+
 def test_step_and_request_calls_reject_null_handles_without_gpu(built):
     for call in (lambda: bc.bc_step_launch(None, 0), lambda: bc.bc_step_sync(None, 0),
                  lambda: bc.bc_step_destroy(None), lambda: bc.bc_step_create(None, 0, 0, 1.0, 0)):
