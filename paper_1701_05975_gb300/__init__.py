@@ -296,6 +296,20 @@ def bc_compute_noalloc(d_row_ptr: int, d_col_idx: int, d_w: int, n: int, nnz: in
 # ------------------------------------------------------------ convenience
 
 
+def _dptr(x) -> int:
+    return 0 if x is None else int(x.data_ptr() if hasattr(x, "data_ptr") else x)
+
+
+def _numel(x) -> int:
+    return 0 if x is None else int(x.numel() if hasattr(x, "numel") else len(x))
+
+
+def _sptr(stream) -> int:
+    if stream is None:
+        return 0
+    return int(stream.cuda_stream if hasattr(stream, "cuda_stream") else stream)
+
+
 class Graph:
     """Owns a device-resident graph (bc_graph_create / bc_graph_destroy)."""
 
@@ -330,6 +344,31 @@ class Graph:
     def autotune(self, sources):
         bc_autotune(self.handle, sources)
 
+    # ---- device buffers (torch tensors or anything with data_ptr()) ---------
+    # Argument marshalling only: every step runs in the library's kernels.
+
+    def compute_async(self, d_sources, d_out, scale: float = 1.0, stream=None):
+        """BC into the device array d_out[n] for the device uint32/int32 ids
+        d_sources[k], enqueued on `stream` (a torch.cuda.Stream, a raw
+        cudaStream_t integer, or None for the legacy default stream)."""
+        bc_compute_async(self.handle, _dptr(d_sources), _numel(d_sources), scale, _dptr(d_out), _sptr(stream))
+
+    def edge_compute_async(self, d_sources, d_out_ebc, d_out_bc, scale: float = 1.0, stream=None):
+        bc_edge_compute_async(self.handle, _dptr(d_sources), _numel(d_sources), scale, _dptr(d_out_ebc),
+                              _dptr(d_out_bc), _sptr(stream))
+
+    def sync(self, stream=None):
+        """Wait for `stream` and raise BCError for a device-side failure of the last async run on it."""
+        bc_sync_status(self.handle, _sptr(stream))
+
+    def step(self, d_sources, d_out, scale: float = 1.0) -> "Step":
+        """One batched run over d_sources captured as a CUDA graph (see Step)."""
+        return Step(self, d_sources, d_out, scale)
+
+    def submit(self, sources, scale: float = 1.0) -> "Request":
+        """Queue a request on the serving loop; the result is a host array."""
+        return Request(self, sources, scale)
+
     def close(self):
         if self.handle is not None:
             bc_graph_destroy(self.handle)
@@ -340,3 +379,53 @@ class Graph:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Step:
+    """A batched run captured once as a CUDA graph (bc_step_create) over the
+    device buffers given at creation; launch() replays it, sync() waits and
+    raises on a device-side failure.  The buffers must outlive the step."""
+
+    def __init__(self, graph: Graph, d_sources, d_out, scale: float = 1.0):
+        self._keep = (graph, d_sources, d_out)
+        self.handle = bc_step_create(graph.handle, _dptr(d_sources), _numel(d_sources), scale, _dptr(d_out))
+
+    def launch(self, stream=None):
+        bc_step_launch(self.handle, _sptr(stream))
+
+    def sync(self, stream=None):
+        bc_step_sync(self.handle, _sptr(stream))
+
+    def close(self):
+        if self.handle is not None:
+            bc_step_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Request:
+    """A request on the serving loop (bc_request_submit); result() waits and
+    returns the host BC array."""
+
+    def __init__(self, graph: Graph, sources, scale: float = 1.0):
+        self.out = np.empty(graph.n, np.float64)
+        self._graph = graph
+        self._done = False
+        self.id = bc_request_submit(graph.handle, sources, scale, self.out)
+
+    def poll(self) -> int:
+        return bc_request_poll(self.id)
+
+    def cancel(self):
+        bc_request_cancel(self.id)
+
+    def result(self, timeout_ms: int = -1) -> np.ndarray:
+        if not self._done:  # the library forgets a request once it has been waited for
+            bc_request_wait(self.id, timeout_ms)
+            self._done = True
+        return self.out

@@ -120,3 +120,29 @@ def test_bad_source_is_reported_and_the_step_recovers():
             bc.bc_step_destroy(step)
         with pytest.raises(bc.BCError):
             bc.bc_step_create(G.handle, d_src.data_ptr(), len(src), 1.0, 0)
+
+
+def test_python_conveniences_marshal_to_the_same_calls():
+    g = gen.er_graph(400, 2000, 1, 30, seed=95)
+    src = gen.sample_sources(g.n, 50, seed=96)
+    want = oracle.bc(g, src, 0.5)
+    st = torch.cuda.Stream()
+    with bc.Graph(g) as G:
+        d_src = dev_sources(src)
+        d_out = torch.empty(g.n, dtype=torch.float64, device="cuda")
+        G.compute_async(d_src, d_out, 0.5, stream=st)
+        G.sync(st)
+        assert_bc_close(d_out.cpu().numpy(), want)
+        d_ebc = torch.empty(g.nnz, dtype=torch.float64, device="cuda")
+        G.edge_compute_async(d_src, d_ebc, d_out, 0.5, stream=st)
+        G.sync(st)
+        assert_bc_close(d_ebc.cpu().numpy(), oracle.edge_bc(g, src, 0.5))
+        with G.step(d_src, d_out, 0.5) as step:
+            for _ in range(2):
+                step.launch(st)
+            step.sync(st)
+            assert_bc_close(d_out.cpu().numpy(), want)
+        reqs = [G.submit(src, 0.5) for _ in range(3)]
+        for r in reqs:
+            assert_bc_close(r.result(), want)
+            assert_bc_close(r.result(), want)  # a second call returns the same array
