@@ -571,7 +571,9 @@ def main():
         bc.bc_set_config(bucket_width=args.width)
     if opts.get("algorithm"):
         bc.bc_set_config(algorithm=opts["algorithm"])
+    t0 = time.perf_counter()
     G = bc.Graph(g, flags=bc.BC_DIRECTED if opts.get("directed") else 0)
+    prep_s = time.perf_counter() - t0  # graph prep: validation, relabeling, upload, packing, Delta_node
     probe = args.autotune if args.autotune >= 0 else min(len(sources), 2048)
     tune_s = 0.0
     if probe:
@@ -668,6 +670,7 @@ def main():
                    "team_threads": int(st.team_threads), "slots": int(st.slots),
                    "bucket_width": int(st.bucket_width), "parallelism": f"replicas x{ws}",
                    "autotune": {"probe_sources": probe, "seconds": round(tune_s, 2)},
+                   "graph_prep_s": round(prep_s, 3),
                    "launch": "CUDA graph (bc_step_launch)" if use_graph else (
                        "bc_edge_compute_async per step" if edge else "bc_compute_async per step"),
                    "algorithm": "delta-stepping" if int(st.algorithm) == 2 else "strict",
