@@ -235,7 +235,8 @@ RunCfg resolve(const bc_graph* g) {
   bc_config c = config_snapshot();
   RunCfg r;
   r.mode = c.mode;
-  const double avg_deg = g->n ? (double)g->nnz / g->n : 0.0;
+  // entries walked per vertex: a directed graph's batches walk in- and out-edges
+  const double avg_deg = g->n ? (double)g->nnz * (g->directed ? 2.0 : 1.0) / g->n : 0.0;
   // measured defaults: the widest CTA teams for dense skewed graphs (large
   // frontiers per batch; half as many sources in flight keeps more of each
   // source's distance array in L2), 128-thread teams for sparse high-diameter
