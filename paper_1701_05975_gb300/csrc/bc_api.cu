@@ -143,6 +143,7 @@ struct bc_graph {
   uint32_t n = 0;
   uint64_t nnz = 0;
   uint32_t max_w = 0;
+  uint64_t width_default = 1;  // mean over non-empty rows of the row's smallest weight (Delta_node)
   int dist_bits = 64;
   int sm_count = 0;
   uint64_t* row_ptr = nullptr;
@@ -246,7 +247,7 @@ RunCfg resolve(const bc_graph* g) {
   r.team = c.team_threads ? c.team_threads : (g->tuned.team ? g->tuned.team : team_default);
   if (r.team == 1024 && g->dist_bits != 32) r.team = 512;  // 1024-thread teams hold 32-bit distances only
   r.width = c.bucket_width ? c.bucket_width
-                           : (g->tuned.width ? g->tuned.width : std::max<uint64_t>(1, g->max_w / 4));
+                           : (g->tuned.width ? g->tuned.width : g->width_default);
   uint32_t si = c.settle_in ? c.settle_in : (g->tuned.settle_in ? g->tuned.settle_in : 1u);
   r.settle_in = (si == 1u) ? 1u : 0u;
   // phases <= n (each settles at least the smallest candidate), refills that
@@ -849,6 +850,20 @@ int bc_graph_create(const uint64_t* row_ptr, const uint32_t* col_idx, const uint
   g->n = n;
   g->nnz = nnz;
   g->max_w = max_w;
+  {
+    // default split width: the mean Delta_node (measured against max_w / 4:
+    // BA 65k +36%, grid +1%, R-MAT +0.3%, ER 1k -8%)
+    double sum = 0.0;
+    uint64_t rows = 0;
+    for (uint32_t v = 0; v < n; ++v) {
+      if (row_ptr[v + 1] == row_ptr[v]) continue;
+      uint32_t m = 0xffffffffu;
+      for (uint64_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) m = std::min(m, w[e]);
+      sum += m;
+      ++rows;
+    }
+    g->width_default = rows ? std::max<uint64_t>(1, (uint64_t)(sum / (double)rows + 0.5)) : 1;
+  }
   g->dist_bits = ((uint64_t)n * std::max<uint32_t>(max_w, 1) * 2ull < 0xffffffffull) ? 32 : 64;
   g->fingerprint = fingerprint(n, nnz, row_ptr, col_idx, w);
   {
