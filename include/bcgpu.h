@@ -92,20 +92,24 @@ typedef uint64_t bc_request_t;
 typedef struct bc_config {
   uint32_t mode;          /* BC_MODE_BATCHED or BC_MODE_PLAIN */
   uint32_t team_threads;  /* threads that share one source: 32 (warp team) or 128/256/512/1024 (CTA team);
-                             1024 needs 32-bit distances and falls back to 512 otherwise */
+                             1024 needs 32-bit distances and falls back to 512 otherwise.  0 = tuned value,
+                             else by entries walked per vertex (>= 20: 1024 or 512, >= 6: 256, else 128) */
   uint32_t max_slots;     /* cap on sources in flight at once (per-source slabs held in device memory) */
   uint32_t settle_in;     /* 1: settle by the strict OUT criterion (Eq. 2 + Eq. 4) OR the strict IN
                              criterion; 2: OUT only (the paper's criterion alone); 0 = automatic (1) */
-  uint64_t bucket_width;  /* near/far split width, in distance units (>= 1) */
+  uint64_t bucket_width;  /* near/far split width, in distance units (>= 1); 0 = tuned value, else the
+                             mean over non-empty rows of the row's smallest weight (Delta_node) */
   uint64_t phase_cap;     /* device cap on phases + queue refills per source; hitting it returns BC_ERR_TIMEOUT.
                              0 = automatic: 4n + 64, above what any valid input needs (phases <= n,
                              refills <= 3n + 2) */
-  double mem_fraction;    /* share of free device memory the slabs may take (0 < f <= 0.95) */
-  uint32_t warp_degree;   /* forward expansion: rows with at least this many entries get one warp each */
-  uint32_t team_degree;   /* ... and rows with at least this many entries the whole team (>= warp_degree) */
+  double mem_fraction;    /* share of free device memory the slabs may take (0 < f <= 0.95); 0 = 0.6 */
+  uint32_t warp_degree;   /* forward expansion: rows with at least this many entries get one warp each
+                             (0 = 32) */
+  uint32_t team_degree;   /* ... and rows with at least this many entries the whole team (>= warp_degree;
+                             0 = 8 x team_threads) */
   uint32_t algorithm;     /* BC_ALGO_AUTO, BC_ALGO_STRICT or BC_ALGO_DELTA (batched mode) */
   uint32_t hot_vertices;  /* on degree-relabeled graphs, the distance words of this many leading (highest-
-                             degree) vertex ids are gathered with an L2 evict-last hint; 0 = automatic */
+                             degree) vertex ids are gathered with an L2 evict-last hint; 0 = 32768 */
 } bc_config;
 
 /* Read the current process-wide configuration. */
