@@ -190,6 +190,28 @@ def test_edge_bc_async_device_buffers():
                 bc.bc_edge_compute_async(G.handle, d_src.data_ptr(), len(src), 0.5, 0, d_bc.data_ptr(), st.cuda_stream)
 
 
+def test_batches_equal_the_paper_replay_with_an_unbounded_split():
+    # with the split width unbounded every candidate sits in the near queue,
+    # so the threshold is exactly Eq. 2's Delta_i; with the OUT test alone
+    # (Eq. 4) the kernel must settle exactly the batches of the oracle's
+    # sequential replay of Algorithm 2, vertex by vertex
+    rng = np.random.default_rng(808)
+    graphs = [gen.random_small_graph(int(rng.integers(2, 60)), 0.15, 1, int(rng.choice([3, 40])), rng)
+              for _ in range(8)]
+    graphs += [gen.er_graph(800, 4000, 1, 50, seed=81), gen.ba_graph(1500, 3, 1, 200, seed=82),
+               gen.grid_graph(20, 25, wmin=1, wmax=9, seed=83)]
+    for team in (128, 1024):
+        bc.bc_set_config(team_threads=team, bucket_width=1 << 40, settle_in=2)
+        for g in graphs:
+            with bc.Graph(g) as G:
+                for s in (0, g.n // 3, g.n - 1):
+                    d, _, lev = G.sssp_debug(s)
+                    d_ref, _, lev_ref, _, _ = oracle.phased(g, s)
+                    reached = d_ref != U64MAX
+                    assert np.array_equal(d, d_ref)
+                    assert np.array_equal(lev[reached], lev_ref[reached]), (g.n, s, team)
+
+
 def test_default_cap_covers_tiny_split_widths():
     # a split width far below the weights makes almost every vertex its own
     # near-queue refill and second-level refill: phases + refills reach ~3n,
