@@ -91,6 +91,11 @@ __device__ __forceinline__ uint64_t atomic_min_d(uint64_t* p, uint64_t v) {
   return (uint64_t)atomicMin(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
 }
 
+// FAR_LEVELS split widths, saturating (a caller may set any width)
+__device__ __forceinline__ uint64_t far_span(uint64_t width) {
+  return width > ~0ull / FAR_LEVELS ? ~0ull : FAR_LEVELS * width;
+}
+
 template <typename D>
 __device__ __forceinline__ D sat_add(D a, uint64_t b) {
   uint64_t lim = (uint64_t)dinf<D>() - 1;
@@ -808,7 +813,7 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
     sh.pair_over = 0;
     sh.stop = 0;
     sh.split = sat_add<D>((D)0, a.width);
-    sh.split2 = sat_add<D>((D)0, (uint64_t)FAR_LEVELS * a.width);
+    sh.split2 = sat_add<D>((D)0, far_span(a.width));
     sh.staged = 0;
   }
   team_sync<TEAM>();
@@ -850,7 +855,7 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
           }
         }
         team_min2<D, TEAM>(lo, dummy, sh.red);
-        const D ns2 = (lo == INF) ? old2 : sat_add<D>(lo, (uint64_t)FAR_LEVELS * a.width);
+        const D ns2 = (lo == INF) ? old2 : sat_add<D>(lo, far_span(a.width));
         uint32_t kept = 0;
         for (uint32_t base = 0; base < fl2; base += TEAM) {
           const uint32_t j = base + t;

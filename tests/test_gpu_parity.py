@@ -212,6 +212,17 @@ def test_batches_equal_the_paper_replay_with_an_unbounded_split():
                     assert np.array_equal(lev[reached], lev_ref[reached]), (g.n, s, team)
 
 
+def test_extreme_split_widths():
+    rng = np.random.default_rng(66)
+    graphs = [gen.er_graph(500, 2500, 1, 100, seed=61), gen.random_small_graph(120, 0.05, 1, 2**31 - 1, rng)]
+    for width in (1 << 61, (1 << 64) - 1):
+        bc.bc_set_config(bucket_width=width)
+        for g in graphs:
+            src = np.arange(0, g.n, 7, dtype=np.uint32)
+            with bc.Graph(g) as G:
+                assert_bc_close(G.compute(src, 0.5), oracle.bc(g, src, 0.5))
+
+
 def test_default_cap_covers_tiny_split_widths():
     # a split width far below the weights makes almost every vertex its own
     # near-queue refill and second-level refill: phases + refills reach ~3n,
