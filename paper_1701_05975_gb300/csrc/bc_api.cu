@@ -329,16 +329,30 @@ int ws_acquire(bc_graph* g, uint32_t slots, uint32_t k, cudaStream_t st, Workspa
   }
   if (w->src_cap < k) {
     // previous uses of this workspace are ordered before st; free is safe after a sync
+    cudaError_t e = cudaSuccess;
     if (w->src) {
-      CK(cudaStreamSynchronize(st));
-      cudaFree(w->src);
-      cudaFreeHost(w->host_src);
-      w->src = nullptr;
-      w->host_src = nullptr;
+      e = cudaStreamSynchronize(st);
+      if (e == cudaSuccess) {
+        cudaFree(w->src);
+        cudaFreeHost(w->host_src);
+        w->src = nullptr;
+        w->host_src = nullptr;
+        w->src_cap = 0;
+      }
     }
     const uint32_t cap = std::max<uint32_t>(k, 1024);
-    CK(cudaMalloc(&w->src, (size_t)cap * 4));
-    CK(cudaMallocHost(&w->host_src, (size_t)cap * 4));
+    if (e == cudaSuccess) e = cudaMalloc(&w->src, (size_t)cap * 4);
+    if (e == cudaSuccess) e = cudaMallocHost(&w->host_src, (size_t)cap * 4);
+    if (e != cudaSuccess) {
+      // hand the workspace back (without a source buffer) so the pool stays usable
+      if (w->src && !w->host_src) {
+        cudaFree(w->src);
+        w->src = nullptr;
+      }
+      std::lock_guard<std::mutex> lk(g->mu);
+      w->busy = false;
+      return cuda_fail(e, "workspace source buffer");
+    }
     w->src_cap = cap;
   }
   *out = w;
@@ -570,10 +584,11 @@ int compute_sync(bc_graph* g, const uint32_t* sources, uint32_t k, double scale,
   if (e == cudaSuccess && out_ebc && g->nnz)
     e = cudaMemcpyAsync(out_ebc, d_ebc, (size_t)g->nnz * 8, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  const Ctl c = *w->host_ctl;  // read before the workspace goes back to the pool
   ws_release(g, w, st);
   if (e != cudaSuccess) return cuda_fail(e, "batched run");
-  record_stats(g, *w->host_ctl, r, slots);
-  return status_from_dev(w->host_ctl->err);
+  record_stats(g, c, r, slots);
+  return status_from_dev(c.err);
 }
 
 int compute_plain(bc_graph* g, const uint32_t* sources, uint32_t k, double scale, double* out_bc, const RunCfg& r) {
@@ -949,7 +964,7 @@ int bc_graph_destroy(bc_graph_t g) {
   if (g->serving_refs.load() > 0) return fail(BC_ERR_BUSY, "graph still has serving requests");
   if (g->step_refs.load() > 0) return fail(BC_ERR_BUSY, "graph still has step graphs (bc_step_destroy them first)");
   cudaSetDevice(g->device);
-  cudaStreamSynchronize(g->stream);
+  cudaDeviceSynchronize();  // async runs on callers' streams may still use the graph's workspaces
   for (auto& w : g->pool) {
     if (w->done) cudaEventSynchronize(w->done);
     ws_free(w.get());
@@ -1015,6 +1030,18 @@ int compute_async(bc_graph* g, const uint32_t* d_sources, uint32_t k, double sca
   if (d_out_ebc)
     if (int rc = ensure_edge_map(g)) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // the workspace this stream kept from its previous async call: that run
+  // and its status copy are ordered before this one on the stream
+  Workspace* prev = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g->mu);
+    auto it = g->async_ws.find(st);
+    if (it != g->async_ws.end()) {
+      prev = it->second;
+      g->async_ws.erase(it);
+    }
+  }
+  if (prev) ws_release(g, prev, st);
   uint32_t slots = 0;
   int rc = plan_slots(g, r, k, &slots);
   if (rc) return rc;
@@ -1025,16 +1052,19 @@ int compute_async(bc_graph* g, const uint32_t* d_sources, uint32_t k, double sca
     cudaError_t e = cudaMemcpyAsync(w->host_ctl, w->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemcpyAsync(control)");
   }
-  {
-    std::lock_guard<std::mutex> lk(g->mu);
-    g->async_ws[st] = w;
-    g->last.algorithm = r.algo == ALGO_DELTA ? BC_ALGO_DELTA : BC_ALGO_STRICT;
-    g->last.team_threads = r.team;
-    g->last.slots = slots;
-    g->last.bucket_width = r.width;
+  if (rc) {
+    ws_release(g, w, st);
+    return rc;
   }
-  ws_release(g, w, st);
-  return rc;
+  // the workspace stays with this stream until bc_sync_status (or the
+  // stream's next async call) has read its status block
+  std::lock_guard<std::mutex> lk(g->mu);
+  g->async_ws[st] = w;
+  g->last.algorithm = r.algo == ALGO_DELTA ? BC_ALGO_DELTA : BC_ALGO_STRICT;
+  g->last.team_threads = r.team;
+  g->last.slots = slots;
+  g->last.bucket_width = r.width;
+  return BC_OK;
 }
 
 }  // namespace
@@ -1061,12 +1091,16 @@ int bc_sync_status(bc_graph_t g, void* stream) {
   {
     std::lock_guard<std::mutex> lk(g->mu);
     auto it = g->async_ws.find(st);
-    if (it != g->async_ws.end()) w = it->second;
+    if (it != g->async_ws.end()) {
+      w = it->second;
+      g->async_ws.erase(it);
+    }
   }
   if (!w) return BC_OK;
+  const Ctl c = *w->host_ctl;  // read before the workspace goes back to the pool
+  ws_release(g, w, st);
   {
     std::lock_guard<std::mutex> lk(g->mu);
-    const Ctl& c = *w->host_ctl;
     g->last.sources = c.stats[STAT_SOURCES];
     g->last.phases = c.stats[STAT_PHASES];
     g->last.refills = c.stats[STAT_REFILLS];
@@ -1083,7 +1117,7 @@ int bc_sync_status(bc_graph_t g, void* stream) {
     g->last.far_scanned = c.stats[STAT_FAR_SCANNED];
     g->last.levels = c.stats[STAT_LEVELS];
   }
-  return status_from_dev(w->host_ctl->err);
+  return status_from_dev(c.err);
 }
 
 int bc_edge_compute(bc_graph_t g, const uint32_t* sources, uint32_t k, double scale, double* out_ebc,
@@ -1135,11 +1169,12 @@ int bc_sssp_debug(bc_graph_t g, uint32_t s, uint64_t* out_dist, double* out_sigm
   // restore the slab invariant (forward-only runs leave distances behind)
   if (e == cudaSuccess) e = cudaMemsetAsync(base + w->lay.off_d, 0xff, dbuf.size(), st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  const Ctl c = *w->host_ctl;  // read before the workspace goes back to the pool
   ws_release(g, w, st);
   if (e != cudaSuccess) return cuda_fail(e, "bc_sssp_debug");
-  if ((rc = status_from_dev(w->host_ctl->err))) return rc;
-  const uint32_t nlev = w->host_ctl->debug[0];
-  const uint32_t reached = w->host_ctl->debug[1];
+  if ((rc = status_from_dev(c.err))) return rc;
+  const uint32_t nlev = c.debug[0];
+  const uint32_t reached = c.debug[1];
   std::vector<uint32_t> level(n, 0xffffffffu);
   for (uint32_t l = 0; l < nlev; ++l)
     for (uint32_t i = ends[l]; i < ends[l + 1] && i < reached; ++i) level[S[i]] = l;

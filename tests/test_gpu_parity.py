@@ -171,6 +171,37 @@ def test_edge_bc_matches_oracle():
     assert_bc_close(vbc, oracle.bc(g, src, 0.5))
 
 
+def test_async_status_stays_with_its_stream():
+    # two streams on one graph: each stream's status (an invalid source on one
+    # of them) must come back to that stream's bc_sync_status, repeatedly
+    torch = pytest.importorskip("torch")
+    g = gen.er_graph(2000, 12000, 1, 50, seed=31)
+    good = gen.sample_sources(g.n, 200, seed=32)
+    bad = good.copy()
+    bad[7] = g.n
+    want = oracle.bc(g, good, 1.0)
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    with bc.Graph(g) as G:
+        d_good = torch.from_numpy(good.astype(np.int32)).cuda()
+        d_bad = torch.from_numpy(bad.astype(np.int32)).cuda()
+        out_a = torch.empty(g.n, dtype=torch.float64, device="cuda")
+        out_b = torch.empty(g.n, dtype=torch.float64, device="cuda")
+        for it in range(4):
+            G.compute_async(d_bad, out_a, 1.0, stream=sa)
+            G.compute_async(d_good, out_b, 1.0, stream=sb)
+            order = (sa, sb) if it % 2 else (sb, sa)
+            for st in order:
+                if st is sa:
+                    with pytest.raises(bc.BCError) as ei:
+                        G.sync(sa)
+                    assert ei.value.code == bc.BC_ERR_INVALID
+                else:
+                    G.sync(sb)
+            assert_bc_close(out_b.cpu().numpy(), want)
+        G.sync(sa)  # nothing pending any more on either stream
+        G.sync(sb)
+
+
 def test_edge_bc_async_device_buffers():
     torch = pytest.importorskip("torch")
     for g, flags, ref in ((gen.er_graph(300, 1200, 1, 5, seed=12), 0, oracle.bc),
