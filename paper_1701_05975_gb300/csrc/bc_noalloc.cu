@@ -13,7 +13,10 @@
 // as an address: once per device, with that device current, it asks the
 // runtime for the array's device address (cudaGetSymbolAddress) and passes that
 // pointer to the kernels.  The first call on a device does this set-up, so it
-// should come before any stream capture.
+// should come before any stream capture.  The address is cached per device
+// together with the unique id of the context it was looked up in; a call
+// that finds another context current (for example after cudaDeviceReset)
+// looks the address up again.
 //
 // All calls share the array, and it keeps whatever the last call left there.
 // Each call therefore re-initialises what must start at a known value: the
@@ -37,14 +40,60 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[BC_NOALLOC_SCRA
 
 constexpr int kMaxDevices = 64;
 std::mutex g_na_mu;
-char* g_na_ptr[kMaxDevices] = {nullptr};
+
+// The scratch array's device address on each device, and the unique id of the
+// context it was looked up in (0: unknown, look it up again).
+struct NaAddr {
+  unsigned long long ctx_id;
+  char* ptr;
+};
+NaAddr g_na_addr[kMaxDevices] = {};
+
+// cuCtxGetCurrent and cuCtxGetId, reached through the runtime's driver entry
+// point query so the library needs no link-time dependency on the driver.
+using CtxGetCurrentFn = int (*)(void** ctx);
+using CtxGetIdFn = int (*)(void* ctx, unsigned long long* id);
+
+// Unique id of the calling thread's current context, or 0 when none is
+// current yet or the driver does not offer the query.
+unsigned long long current_ctx_id() {
+  static const CtxGetCurrentFn get_cur = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<CtxGetCurrentFn>(f);
+  }();
+  static const CtxGetIdFn get_id = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<CtxGetIdFn>(f);
+  }();
+  if (!get_cur || !get_id) return 0;
+  void* ctx = nullptr;
+  if (get_cur(&ctx) != 0 || !ctx) return 0;
+  unsigned long long id = 0;
+  if (get_id(ctx, &id) != 0) return 0;
+  return id;
+}
 
 struct NaCtl {
   uint32_t counter;
   int err;
   uint32_t debug[2];
   unsigned long long stats[STAT_COUNT];
+  // sums over all entries (v -> u, w) of hash(v, u, w) and of hash(u, v, w):
+  // equal for a symmetric CSR (the two multisets are the same)
+  unsigned long long sym[2];
 };
+
+// The device status word carries DEV_* codes; the caller reads them as BC_* codes.
+static_assert(DEV_OK == BC_OK && DEV_ERR_INVALID == BC_ERR_INVALID && DEV_ERR_TIMEOUT == BC_ERR_TIMEOUT,
+              "device status codes must equal the ABI codes they are reported as");
 
 constexpr uint64_t kCtlBytes = 256;
 static_assert(sizeof(NaCtl) <= kCtlBytes, "control block must fit its reserved bytes");
@@ -83,10 +132,25 @@ SlabLayout na_layout(uint32_t n) {
   return L;
 }
 
+// 64-bit finaliser of SplitMix64 (Steele, Lea and Flood, "Fast splittable
+// pseudorandom number generators", OOPSLA 2014).
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+// Hash of one directed entry (a -> b, weight w).
+__device__ __forceinline__ uint64_t entry_hash(uint32_t a, uint32_t b, uint32_t w) {
+  return mix64((((uint64_t)a << 32) | b) ^ mix64((uint64_t)w + 0x9e3779b97f4a7c15ull));
+}
+
 // Validates the caller's CSR while packing it (every read stays inside the
 // caller's arrays whatever their contents) and computes Delta_node.  On any
 // violation it records DEV_ERR_INVALID and parks the source counter far above
-// any source index, so the batched kernel that follows does no work.
+// any source index, so the batched kernel that follows does no work.  It also
+// sums, mod 2^64, a hash of every entry (v -> u, w) and of its reverse
+// (u -> v, w); na_check_symmetry compares the two sums.
 __global__ void na_validate_prep(uint32_t n, uint64_t nnz, const uint64_t* __restrict__ row_ptr,
                                  const uint32_t* __restrict__ col, const uint32_t* __restrict__ w,
                                  const uint32_t* __restrict__ src, uint32_t k, uint2* __restrict__ adj,
@@ -94,6 +158,7 @@ __global__ void na_validate_prep(uint32_t n, uint64_t nnz, const uint64_t* __res
   const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   const uint64_t nth = (uint64_t)gridDim.x * blockDim.x;
   bool bad = false;
+  unsigned long long fwd = 0, rev = 0;
   if (tid == 0 && (row_ptr[0] != 0 || row_ptr[n] != nnz)) bad = true;
   for (uint64_t v = tid; v < n; v += nth) {
     const uint64_t r0 = row_ptr[v], r1 = row_ptr[v + 1];
@@ -106,13 +171,33 @@ __global__ void na_validate_prep(uint32_t n, uint64_t nnz, const uint64_t* __res
         if (c >= n || ww == 0) bad = true;
         adj[e] = make_uint2(c < n ? c : 0u, ww);
         m = min(m, ww);
+        fwd += entry_hash((uint32_t)v, c, ww);
+        rev += entry_hash(c, (uint32_t)v, ww);
       }
     }
     dnode[v] = m;
   }
   for (uint64_t i = tid; i < k; i += nth)
     if (src[i] >= n) bad = true;
+  for (int o = 16; o > 0; o >>= 1) {
+    fwd += __shfl_xor_sync(0xffffffffu, fwd, o);
+    rev += __shfl_xor_sync(0xffffffffu, rev, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&ctl->sym[0], fwd);
+    atomicAdd(&ctl->sym[1], rev);
+  }
   if (bad) {
+    atomicCAS(&ctl->err, DEV_OK, DEV_ERR_INVALID);
+    atomicExch(&ctl->counter, 0x80000000u);
+  }
+}
+
+// An asymmetric CSR (some entry without its reverse entry of the same
+// weight) makes the two hash sums differ; it is then rejected like any other
+// invalid input.  Single thread.
+__global__ void na_check_symmetry(NaCtl* ctl) {
+  if (ctl->sym[0] != ctl->sym[1]) {
     atomicCAS(&ctl->err, DEV_OK, DEV_ERR_INVALID);
     atomicExch(&ctl->counter, 0x80000000u);
   }
@@ -152,14 +237,18 @@ extern "C" int bc_compute_noalloc(const uint64_t* d_row_ptr, const uint32_t* d_c
   if (dev < 0 || dev >= kMaxDevices) return na_fail(BC_ERR_INVALID, "bc_compute_noalloc: device index too large");
   char* base = nullptr;
   {
+    // set-up, once per device and context: the array's device address
     std::lock_guard<std::mutex> lk(g_na_mu);
-    if (!g_na_ptr[dev]) {
+    NaAddr& ad = g_na_addr[dev];
+    const unsigned long long cur = current_ctx_id();
+    if (!ad.ptr || cur == 0 || cur != ad.ctx_id) {
       void* p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // makes the device's context current if needed
       if (e != cudaSuccess) return na_fail(BC_ERR_CUDA, cudaGetErrorString(e));
-      g_na_ptr[dev] = static_cast<char*>(p);
+      ad.ptr = static_cast<char*>(p);
+      ad.ctx_id = current_ctx_id();
     }
-    base = g_na_ptr[dev];
+    base = ad.ptr;
   }
   int sms = 0;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -188,6 +277,10 @@ extern "C" int bc_compute_noalloc(const uint64_t* d_row_ptr, const uint32_t* d_c
     const int grid = (int)std::min<uint64_t>((work + 255) / 256, (uint64_t)sms * 8);
     na_validate_prep<<<std::max(grid, 1), 256, 0, st>>>(n, nnz, d_row_ptr, d_col_idx, d_w, d_sources, k, adj, dnode,
                                                         ctl);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    na_check_symmetry<<<1, 1, 0, st>>>(ctl);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = launch_fill_slabs(slabs, lay.stride, (uint32_t)slots, lay.off_d, al256((uint64_t)n * 8),

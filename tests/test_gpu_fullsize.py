@@ -1,11 +1,21 @@
 """Full-size workloads in the launch configuration the benchmark times.
 
-At these sizes the oracle cannot redo every source, so each workload is
-checked three ways: (1) the full launch against the sum of launches over a
-partition of its source list (BC is additive over sources; this holds at any
-size), (2) the GPU against the oracle on a sample of sources, over all n
-outputs, and (3) bit-exact distances and sigma for sampled sources.
+Each benchmark workload (ER 1k, BA 65k, R-MAT scale 20, the 1024 x 1024 grid)
+runs exactly as `bench.py` times it: autotuned on a 2048-source probe, then
+one batched run over the whole source list captured as a CUDA graph and
+replayed.  That output is compared with the CPU oracle over the WHOLE source
+list (every source, all n outputs, relative error 1e-9 and the exact zero
+pattern; Eq. 1 with the sampled scale).  The oracle runs on every host core
+in a background thread while the GPU works.  Also: the full launch against
+the sum of launches over a partition of its source list (BC is additive over
+sources), and bit-exact distances and sigma for a few sources.  A prefix of
+the serving stream (every graph size, including the 65k and 262k-vertex
+graphs) is checked request by request against the oracle.
 """
+import concurrent.futures
+import os
+import time
+
 import numpy as np
 import pytest
 
@@ -15,6 +25,7 @@ from paper_1701_05975_gb300 import gen
 
 pytestmark = pytest.mark.gpu
 REL = 1e-9
+CORES = os.cpu_count() or 1
 
 
 def assert_close(got, want, rel=REL):
@@ -23,6 +34,32 @@ def assert_close(got, want, rel=REL):
     if nz.any():
         err = np.abs(got[nz] - want[nz]) / np.abs(want[nz])
         assert err.max() <= rel, err.max()
+
+
+class Background:
+    """One oracle job on a worker thread (the C oracle releases the GIL), so
+    the host cores compute the expected values while the GPU runs."""
+
+    def __init__(self, fn, *args, **kw):
+        self._ex = concurrent.futures.ThreadPoolExecutor(max_workers=1)
+        self._t0 = time.perf_counter()
+        self._fut = self._ex.submit(fn, *args, **kw)
+
+    def result(self):
+        try:
+            out = self._fut.result()
+        finally:
+            self._ex.shutdown(wait=True)
+        print(f"oracle: {time.perf_counter() - self._t0:.1f} s on {CORES} host threads")
+        return out
+
+
+def oracle_split(fn, g, sources, scale):
+    """A single-threaded oracle form over `sources`, one chunk per host core."""
+    chunks = [c for c in np.array_split(np.asarray(sources, np.uint32), CORES) if len(c)]
+    with concurrent.futures.ThreadPoolExecutor(max_workers=len(chunks)) as ex:
+        parts = list(ex.map(lambda c: fn(g, c, scale), chunks))
+    return np.sum(parts, axis=0)
 
 
 def run_async(G, n, sources, scale):
@@ -53,7 +90,10 @@ def run_step(G, n, sources, scale, launches=2):
     return d_out.cpu().numpy()
 
 
-def check_workload(g, sources, scale, parts, n_oracle, n_debug, tune=False):
+def check_workload(g, sources, scale, parts, n_debug, tune=True):
+    """The benchmark's exact run of one workload against the oracle over the
+    whole source list."""
+    want = Background(oracle.bc, g, sources, scale, nthreads=CORES)
     with bc.Graph(g) as G:
         if tune:  # the benchmark tunes on a 2048-source probe before it times
             G.autotune(sources[:2048])
@@ -65,18 +105,14 @@ def check_workload(g, sources, scale, parts, n_oracle, n_debug, tune=False):
             total += run_async(G, g.n, chunk, scale)
         assert_close(full, total, rel=1e-11)
         assert_close(run_async(G, g.n, sources, scale), full, rel=1e-11)
-        # oracle on a sample of sources that reach most of the graph
         deg = g.degrees()
-        sample = [int(s) for s in sources if deg[s] > 0][:n_oracle]
-        got = run_async(G, g.n, np.array(sample, np.uint32), 1.0)
-        want = oracle.bc(g, np.array(sample, np.uint32), 1.0, nthreads=max(1, len(sample)))
-        assert_close(got, want)
-        for s in sample[:n_debug]:
+        for s in [int(x) for x in sources if deg[x] > 0][:n_debug]:
             d, sg, lev = G.sssp_debug(s)
             d_ref, sg_ref, _ = oracle.sssp(g, s)
             assert np.array_equal(d, d_ref)
             assert np.array_equal(sg, sg_ref)
-        return full, stats
+    assert_close(full, want.result())
+    return full, stats
 
 
 def test_rmat20_directed_full_launch():
@@ -90,10 +126,10 @@ def test_rmat20_directed_full_launch():
         for chunk in np.array_split(sources, 4):
             total += run_async(G, g.n, chunk, scale)
         assert_close(full, total, rel=1e-11)
-        # sources with out-edges reach part of the graph; compare every output
+        # 64 sources with out-edges (each reaches part of the graph): every output
         outdeg = np.diff(g.row_ptr)
-        sample = np.array([int(s) for s in sources if outdeg[s] > 0][:6], np.uint32)
-        assert_close(run_async(G, g.n, sample, 1.0), oracle.bc_directed(g, sample, 1.0))
+        sample = np.array([int(s) for s in sources if outdeg[s] > 0][:64], np.uint32)
+        assert_close(run_async(G, g.n, sample, 1.0), oracle_split(oracle.bc_directed, g, sample, 1.0))
         for s in sample[:2]:
             d, sg, _ = G.sssp_debug(int(s))
             d_ref, sg_ref, _ = oracle.sssp(g, int(s))
@@ -123,15 +159,15 @@ def test_rmat20_edge_full_launch():
         assert_close(vbc, run_async(G, g.n, sources, scale), rel=1e-11)
         parts = [run_edge_async(G, g, c, scale)[0] for c in np.array_split(sources, 2)]
         assert_close(ebc, parts[0] + parts[1], rel=1e-11)
-        # a sample of sources: every entry's share against the oracle
+        # 32 sources: every entry's share against the oracle
         deg = g.degrees()
-        sample = np.array([int(s) for s in sources if deg[s] > 0][:4], np.uint32)
-        assert_close(run_edge_async(G, g, sample, 1.0)[0], oracle.edge_bc(g, sample, 1.0))
+        sample = np.array([int(s) for s in sources if deg[s] > 0][:32], np.uint32)
+        assert_close(run_edge_async(G, g, sample, 1.0)[0], oracle_split(oracle.edge_bc, g, sample, 1.0))
 
 
 def test_rmat20_full_launch():
     g, sources, scale = gen.workload_rmat20()
-    full, stats = check_workload(g, sources, scale, parts=4, n_oracle=6, n_debug=2, tune=True)
+    full, stats = check_workload(g, sources, scale, parts=4, n_debug=2)
     assert stats.team_threads == 1024  # the configuration the benchmark measured
     # isolated vertices never lie on a path
     assert np.all(full[g.degrees() == 0] == 0)
@@ -139,9 +175,74 @@ def test_rmat20_full_launch():
 
 def test_grid1024_full_launch():
     g, sources, scale = gen.workload_grid1024()
-    check_workload(g, sources, scale, parts=2, n_oracle=3, n_debug=1)
+    check_workload(g, sources, scale, parts=2, n_debug=1)
 
 
 def test_ba65k_full_launch():
     g, sources, scale = gen.workload_ba65k()
-    check_workload(g, sources, scale, parts=2, n_oracle=16, n_debug=2)
+    check_workload(g, sources, scale, parts=2, n_debug=2)
+
+
+def test_er1k_full_launch():
+    g, sources, scale = gen.workload_er1k()
+    check_workload(g, sources, scale, parts=3, n_debug=4)
+
+
+def serving_prefix(min_requests=100, max_requests=400):
+    """The benchmark's request stream (same generator and seed), cut after at
+    least `min_requests` requests and once every 65k and 262k-vertex graph of
+    the pool has appeared."""
+    reqs = gen.serving_requests(num=2000, rate_per_s=1.0, seed=0)
+    big = {(k, n) for k in gen.SERVING_KINDS for n in gen.SERVING_SIZES if n >= 65536}
+    seen = set()
+    for i, r in enumerate(reqs):
+        seen.add((r.kind, r.n))
+        if i + 1 >= min_requests and big <= seen:
+            return reqs[: i + 1]
+        if i + 1 >= max_requests:
+            break
+    raise AssertionError("the stream prefix misses a large graph")
+
+
+def serving_oracle(pool, reqs):
+    """Expected result of every request: exact requests on one graph share one
+    oracle run (same source list and scale), sampled ones get their own."""
+    cache, out = {}, []
+    for r in reqs:
+        g = pool[(r.kind, r.n)]
+        key = (r.kind, r.n, r.scale, len(r.sources), int(r.sources[0]), int(r.sources[-1]),
+               int(np.sum(r.sources, dtype=np.uint64)))
+        if key not in cache:
+            cache[key] = oracle.bc(g, r.sources, r.scale, nthreads=CORES)
+        out.append(cache[key])
+    return out
+
+
+def test_serving_stream_prefix_against_oracle():
+    reqs = serving_prefix()
+    pool = {}
+    for r in reqs:
+        if (r.kind, r.n) not in pool:
+            pool[(r.kind, r.n)] = gen.serving_graph(r.kind, r.n, seed=0)
+    assert {n for (_, n) in pool} >= {65536, 262144}
+    want = Background(serving_oracle, pool, reqs)
+    graphs = {key: bc.Graph(g) for key, g in pool.items()}
+    try:
+        bc.bc_serving_reset()
+        rng = np.random.default_rng(9)
+        outs, ids = [], []
+        for r in reqs:  # a burst with short random gaps, so requests overlap on the device
+            out = np.full(r.n, -1.0)
+            outs.append(out)
+            ids.append(bc.bc_request_submit(graphs[(r.kind, r.n)].handle, r.sources, r.scale, out))
+            time.sleep(float(rng.exponential(0.001)))
+        for rid in ids:
+            bc.bc_request_wait(rid, 600000)
+        st = bc.bc_serving_stats_get()
+        assert st.completed == len(reqs) and st.failed == 0
+        assert st.max_concurrent >= 2
+    finally:
+        for G in graphs.values():
+            G.close()
+    for r, got, exp in zip(reqs, outs, want.result()):
+        assert_close(got, exp)
