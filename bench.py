@@ -70,19 +70,29 @@ def oracle_fn(opts):
     return None, 0
 
 
+def timing_oracle():
+    """The oracle's C source built for timing (-O3, the host's instruction
+    set): (library, flags)."""
+    import oracle
+
+    lib = oracle.timing_lib()
+    return lib, " ".join(oracle.TIMING_FLAGS)
+
+
 def run_oracle(g, sources, scale, opts, cores):
     """The oracle as it stands over `sources`; single-threaded forms run one
     source chunk per host core (ctypes releases the GIL during each call)."""
     import oracle
 
+    lib, _ = timing_oracle()
     fn, _ = oracle_fn(opts)
     if fn is None:
-        return oracle.bc(g, sources, scale, nthreads=cores)
+        return oracle.bc(g, sources, scale, nthreads=cores, lib=lib)
     import concurrent.futures
 
     chunks = [c for c in np.array_split(np.asarray(sources), cores) if len(c)]
     with concurrent.futures.ThreadPoolExecutor(max_workers=len(chunks)) as ex:
-        parts = list(ex.map(lambda c: fn(g, c, scale), chunks))
+        parts = list(ex.map(lambda c: fn(g, c, scale, lib=lib), chunks))
     return np.sum(parts, axis=0)
 
 
@@ -279,9 +289,18 @@ def cpu_baseline(g, sources, opts=None, seconds_target=15.0, max_sample=4096):
     dt1 = time.perf_counter() - t1
     return {"value": k * m / dt / 1e9, "unit": "GTEPS", "cores": cores, "kind": "oracle",
             "sample": f"first {k} of {len(sources)} sources of the same workload, {dt:.2f} s, "
-                      f"{cores} host threads",
+                      f"{cores} host threads, oracle built with gcc {timing_oracle()[1]}",
             "single_core": {"value": k1 * m / dt1 / 1e9, "unit": "GTEPS",
                             "sample": f"{k1} sources spread over the first {k}, {dt1:.2f} s, one thread"}}
+
+
+def cycle_shares(st):
+    """Fractions of the batched kernel's per-source SM cycles spent in each
+    section (expansion, refills, threshold + settle, backward)."""
+    parts = {"expand": st.cycles_expand, "refill": st.cycles_refill, "settle": st.cycles_settle,
+             "backward": st.cycles_backward}
+    total = sum(parts.values())
+    return {k: round(v / total, 4) for k, v in parts.items()} if total else None
 
 
 def metric_name(opts):
@@ -320,7 +339,8 @@ def run_reference(args, g, sources, scale, desc, opts=None):
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": desc, "n": g.n, "m": m, "sources_per_step": k, "sources_in_workload": len(sources)},
         "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": cores, "kind": "oracle",
-                         "sample": f"first {k} of {len(sources)} sources per step"},
+                         "sample": f"first {k} of {len(sources)} sources per step, oracle built with gcc "
+                                   f"{timing_oracle()[1]}"},
         "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -412,7 +432,7 @@ def run_serving_reference(args, desc):
             pool[key] = gen.serving_graph(r.kind, r.n, seed=0)
         g = pool[key]
         t0 = time.perf_counter()
-        oracle.bc(g, r.sources, r.scale, nthreads=cores)
+        oracle.bc(g, r.sources, r.scale, nthreads=cores, lib=timing_oracle()[0])
         t_total += time.perf_counter() - t0
         done += 1
         edges += len(r.sources) * g.m
@@ -422,20 +442,18 @@ def run_serving_reference(args, desc):
             "ms_per_step": t_total * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "config": {"workload": desc, "requests_timed": done},
             "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": cores, "kind": "oracle",
-                             "sample": f"first {done} of {len(reqs)} requests, run back to back"},
+                             "sample": f"first {done} of {len(reqs)} requests, run back to back, oracle built "
+                                       f"with gcc {timing_oracle()[1]}"},
             "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def run_serving(args, desc):
-    """Serving workload: saturated throughput first (a burst of requests),
-    then a Poisson stream at 0.7 of it; p50/p99 from submit to done."""
-    ws, rank, local = dist_env()
-    import torch
-
+def serving_measure(args):
+    """The serving stream: saturated throughput first (a burst of requests),
+    then the Poisson stream at 0.7 of it; p50/p99 from submit to done.
+    Returns the measurement as a dict (one rank's view)."""
     import paper_1701_05975_gb300 as bc
 
-    torch.cuda.set_device(local)
     pool = {}
     for kind in gen.SERVING_KINDS:
         for n in gen.SERVING_SIZES:
@@ -463,41 +481,58 @@ def run_serving(args, desc):
         makespan = time.perf_counter() - t_start
         return makespan, bc.bc_serving_stats_get()
 
-    # warm-up: one request per graph (workspace allocation)
-    warm = [gen.ServingRequest(0.0, k, n, np.arange(min(n, 64), dtype=np.uint32), 1.0) for (k, n) in pool]
-    run_stream(warm, None)
-    burst = reqs[: min(200, len(reqs))]
-    mk_sat, _ = run_stream(burst, None)
-    sat_rate = len(burst) / mk_sat
-    rate = 0.7 * sat_rate
-    makespan, st = run_stream(reqs, rate)
-    edges = sum(len(r.sources) * pool[(r.kind, r.n)].m for r in reqs)
-    gteps = edges / makespan / 1e9
-    # optional load sweep: shorter streams (the first --sweep-requests
-    # requests) at other fractions of the saturated rate
-    sweep = []
-    for load in ([float(x) for x in args.sweep.split(",")] if args.sweep else []):
-        sub = reqs[: args.sweep_requests]
-        mk, sst = run_stream(sub, load * sat_rate)
-        e = sum(len(r.sources) * pool[(r.kind, r.n)].m for r in sub)
-        sweep.append({"load": load, "requests": len(sub), "gteps": e / mk / 1e9, "p50_ms": sst.p50_ms,
-                      "p99_ms": sst.p99_ms, "mean_ms": sst.mean_ms})
+    try:
+        # warm-up: one request per graph (workspace allocation)
+        warm = [gen.ServingRequest(0.0, k, n, np.arange(min(n, 64), dtype=np.uint32), 1.0) for (k, n) in pool]
+        run_stream(warm, None)
+        burst = reqs[: min(200, len(reqs))]
+        mk_sat, _ = run_stream(burst, None)
+        sat_rate = len(burst) / mk_sat
+        rate = 0.7 * sat_rate
+        makespan, st = run_stream(reqs, rate)
+        edges = sum(len(r.sources) * pool[(r.kind, r.n)].m for r in reqs)
+        gteps = edges / makespan / 1e9
+        # optional load sweep: shorter streams (the first --sweep-requests
+        # requests) at other fractions of the saturated rate
+        sweep = []
+        for load in ([float(x) for x in args.sweep.split(",")] if args.sweep else []):
+            sub = reqs[: args.sweep_requests]
+            mk, sst = run_stream(sub, load * sat_rate)
+            e = sum(len(r.sources) * pool[(r.kind, r.n)].m for r in sub)
+            sweep.append({"load": load, "requests": len(sub), "gteps": e / mk / 1e9, "p50_ms": sst.p50_ms,
+                          "p99_ms": sst.p99_ms, "mean_ms": sst.mean_ms})
+    finally:
+        for G in graphs.values():
+            G.close()
+    return {"gteps": gteps, "makespan_s": makespan, "requests": len(reqs), "arrival_rate_per_s": rate,
+            "saturated_rate_per_s": sat_rate, "load": 0.7,
+            "latency_ms": {"p50": st.p50_ms, "p99": st.p99_ms, "mean": st.mean_ms},
+            "completed": int(st.completed), "failed": int(st.failed), "max_concurrent": int(st.max_concurrent),
+            "sweep": sweep,
+            "h2d_bytes": int(sum(4 * len(r.sources) for r in reqs)),
+            "d2h_bytes": int(sum(8 * r.n for r in reqs))}
+
+
+def run_serving(args, desc):
+    """Serving workload as the headline of its own line."""
+    ws, rank, local = dist_env()
+    import torch
+
+    torch.cuda.set_device(local)
+    sv = serving_measure(args)
     line = {
-        "metric": "serving: aggregate GTEPS and p50/p99 latency (submit -> done)", "value": gteps, "unit": "GTEPS",
-        "n_gpus": ws, "steps": 1, "warmup": 1, "ms_per_step": makespan * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": desc, "requests": len(reqs), "arrival_rate_per_s": rate,
-                   "saturated_rate_per_s": sat_rate, "load": 0.7},
-        "latency_ms": {"p50": st.p50_ms, "p99": st.p99_ms, "mean": st.mean_ms},
-        "completed": int(st.completed), "failed": int(st.failed), "max_concurrent": int(st.max_concurrent),
-        "sweep": sweep,
-        "e2e": {"value": gteps, "unit": "GTEPS", "h2d_bytes_per_step": int(sum(4 * len(r.sources) for r in reqs)),
-                "d2h_bytes_per_step": int(sum(8 * r.n for r in reqs))},
+        "metric": "serving: aggregate GTEPS and p50/p99 latency (submit -> done)", "value": sv["gteps"],
+        "unit": "GTEPS", "n_gpus": ws, "steps": 1, "warmup": 1, "ms_per_step": sv["makespan_s"] * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "requests": sv["requests"], "arrival_rate_per_s": sv["arrival_rate_per_s"],
+                   "saturated_rate_per_s": sv["saturated_rate_per_s"], "load": sv["load"]},
+        "latency_ms": sv["latency_ms"], "completed": sv["completed"], "failed": sv["failed"],
+        "max_concurrent": sv["max_concurrent"], "sweep": sv["sweep"],
+        "e2e": {"value": sv["gteps"], "unit": "GTEPS", "h2d_bytes_per_step": sv["h2d_bytes"],
+                "d2h_bytes_per_step": sv["d2h_bytes"]},
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
-    for G in graphs.values():
-        G.close()
 
 
 def main():
@@ -524,9 +559,13 @@ def main():
                     "({rank} is replaced by the rank)")
     ap.add_argument("--no-graph", action="store_true", help="enqueue each step with bc_compute_async instead of "
                     "replaying a captured step graph")
+    ap.add_argument("--no-serving", action="store_true", help="leave the serving stream (p50/p99 latency, aggregate "
+                    "GTEPS over 2000 requests) out of a single-GPU line of the other workloads")
     args = ap.parse_args()
 
     desc, maker = WORKLOADS[args.workload]
+    if args.impl == "reference" or not args.no_cpu_baseline:
+        timing_oracle()  # compile the timing build of the oracle before any GPU work
     if args.workload == "ablation":
         run_ablation(args, desc)
         return
@@ -668,7 +707,8 @@ def main():
                    "l2": "inputs larger than L2: graph %.0f MB + %d per-source slabs of %.1f MB"
                          % (G.info().device_bytes / 1e6, int(st.slots), G.info().slab_bytes / 1e6),
                    "team_threads": int(st.team_threads), "slots": int(st.slots),
-                   "bucket_width": int(st.bucket_width), "parallelism": f"replicas x{ws}",
+                   "bucket_width": int(st.bucket_width), "warp_degree": int(st.warp_degree),
+                   "team_degree": int(st.team_degree), "parallelism": f"replicas x{ws}",
                    "autotune": {"probe_sources": probe, "seconds": round(tune_s, 2)},
                    "graph_prep_s": round(prep_s, 3),
                    "launch": "CUDA graph (bc_step_launch)" if use_graph else (
@@ -681,11 +721,15 @@ def main():
         "gpu_launches": (2 + (scale != 1.0) * (2 if edge else 1)) * args.steps,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     # ncu-measured DRAM bytes per launch over the same launch time
+                     "frac_measured": (traffic / launch_avg_s / 1e9 / peak) if traffic else None,
                      "alg_bytes_per_launch": alg_bytes, "kernel": "bc_batched_kernel"},
         "clocks": clk,
         "run_stats": {"phases_per_source": st.phases / max(st.sources, 1),
                       "refills_per_source": st.refills / max(st.sources, 1),
-                      "reached_per_source": st.reached / max(st.sources, 1)},
+                      "reached_per_source": st.reached / max(st.sources, 1),
+                      # share of each source's SM cycles (team leader's clock) per section
+                      "cycle_shares": cycle_shares(st)},
     }
     if args.plain_sample and rank == 0 and not edge and not opts.get("directed"):
         sub = sources[: args.plain_sample]
@@ -698,12 +742,22 @@ def main():
         dt = time.perf_counter() - t0
         bc.bc_set_config(c0)
         line["plain"] = {"value": len(sub) * m / dt / 1e9, "unit": "GTEPS", "sources": len(sub)}
+    if step_h is not None:
+        bc.bc_step_destroy(step_h)
+        step_h = None
+    G.close()
+    if ws == 1 and not args.no_serving and args.workload == "rmat20":
+        # the serving half of the metric (p50/p99 latency, aggregate GTEPS),
+        # measured after the batched workload's graph and workspaces are freed
+        sv = serving_measure(args)
+        line["serving"] = {"workload": WORKLOADS["serving"][0], "gteps": sv["gteps"], "unit": "GTEPS",
+                           "latency_ms": sv["latency_ms"], "requests": sv["requests"], "load": sv["load"],
+                           "arrival_rate_per_s": sv["arrival_rate_per_s"],
+                           "saturated_rate_per_s": sv["saturated_rate_per_s"], "completed": sv["completed"],
+                           "failed": sv["failed"], "max_concurrent": sv["max_concurrent"]}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g, sources, opts)
     emit(line, rank)
-    if step_h is not None:
-        bc.bc_step_destroy(step_h)
-    G.close()
     if dist is not None:
         dist.destroy_process_group()
 

@@ -173,6 +173,13 @@ int bc_compute_async(bc_graph_t g, const uint32_t *d_sources, uint32_t k, double
 /*
  * Wait for all work enqueued on `stream` by bc_compute_async for graph g and
  * return the status recorded by its kernels (BC_OK, BC_ERR_TIMEOUT, BC_ERR_INVALID).
+ * Each stream that made an async call on g keeps one of g's workspaces (its
+ * slabs and status block) reserved until this call, or the same stream's next
+ * async call on g, has read that status: call bc_sync_status before
+ * destroying the stream or reusing its handle, or the workspace stays reserved
+ * (and the pool grows by one workspace for each such stream).  If the
+ * synchronisation itself fails, the workspace is released and BC_ERR_CUDA
+ * is returned.
  */
 int bc_sync_status(bc_graph_t g, void *stream);
 
@@ -211,8 +218,16 @@ int bc_compute_paper_variant(bc_graph_t g, const uint32_t *sources, uint32_t k, 
 /*
  * Serving (continuous batching).  Submit copies sources[k] at the call; the
  * HOST array out_bc[n] must stay valid until the request is DONE, FAILED or
- * CANCELLED.  Requests on different graphs and sizes are admitted as device
- * memory and source slots free up and run concurrently on separate streams.
+ * CANCELLED.  Requests on different graphs and sizes are admitted in arrival
+ * order as device memory allows (each holds a workspace for up to as many
+ * sources in flight as the GPU holds for its graph).  Every admitted request
+ * runs as a sequence of source batches (about two waves of its sources in
+ * flight each); a scheduler thread interleaves the batches of all admitted
+ * requests on up to 8 streams, least remaining work first, and re-divides the
+ * GPU's resident threads at every batch among the requests with work left
+ * (at most 4 ways), so batches of different graphs run on the device at the
+ * same time and a large request yields at its batch boundaries.  Not in the
+ * paper: a serving layer around its per-source method.
  * BC_ERR_NOMEM: the request alone can never fit the memory budget.
  * BC_ERR_BUSY: the pending queue is full.
  */
@@ -230,7 +245,9 @@ int bc_request_poll(bc_request_t id, int *out_state);
  */
 int bc_request_wait(bc_request_t id, int timeout_ms);
 
-/* Cancel a QUEUED request (BC_OK) ; a RUNNING one finishes (BC_ERR_BUSY). */
+/* Cancel a request (BC_OK).  A QUEUED one is CANCELLED at once; a RUNNING one
+ * stops at its next source-batch boundary and ends CANCELLED without writing
+ * out_bc; a finished one is left as it is. */
 int bc_request_cancel(bc_request_t id);
 
 /* Serving statistics: requests completed and their latencies (submit -> done). */
@@ -282,15 +299,22 @@ typedef struct bc_run_stats {
   uint64_t far_scanned;     /* far-queue entries read by refills */
   uint64_t levels;          /* backward levels summed over sources (settle batches, or DAG hop depths) */
   uint32_t algorithm;       /* schedule of the run: BC_ALGO_STRICT or BC_ALGO_DELTA */
+  uint32_t warp_degree;     /* degree thresholds of the run's forward expansion: rows with at least */
+  uint32_t team_degree;     /* warp_degree entries got a warp each, with at least team_degree the whole team */
 } bc_run_stats;
 
 int bc_last_run_stats(bc_graph_t g, bc_run_stats *out);
 
 /*
- * Autotuner: times candidate (schedule, team size, bucket width) settings
- * on a probe sample of `sources` (k_probe of them, HOST array) and stores the
- * fastest as the graph's tuned configuration, used whenever the process-wide
- * config leaves a field at 0.  Results are cached per graph fingerprint.
+ * Autotuner: times candidate settings on a probe sample of `sources`
+ * (k_probe of them, HOST array) and stores the fastest as the graph's tuned
+ * configuration, used whenever the process-wide config leaves a field at 0:
+ * team size x bucket width (and the delta-stepping schedule where the strict
+ * one needs 1000 or more phases per source), then the degree thresholds of
+ * the forward expansion (warp_degree in {8, 16, 32, 64}, then team_degree in
+ * {2, 8, 32} x team size; Sec. 3.4 studies the same trade-off as its
+ * WARP_SIZE), then sources in flight (full or half capacity).  Results are
+ * cached per graph fingerprint.
  */
 int bc_autotune(bc_graph_t g, const uint32_t *sources, uint32_t k_probe);
 
@@ -327,7 +351,11 @@ int bc_step_destroy(bc_step_t step);
  *
  * Inputs and outputs are the caller's DEVICE arrays: the CSR of the
  * undirected graph (d_row_ptr[n + 1], d_col_idx[nnz], d_w[nnz], the same
- * conventions as bc_graph_create; the contents are validated on the device),
+ * conventions as bc_graph_create, both directions of every edge stored; the
+ * contents are validated on the device: row_ptr, col_idx < n, w >= 1, every
+ * source < n, and symmetry, by comparing a 64-bit hash sum of all entries
+ * with that of their reverses, so a CSR with a one-way entry is reported as
+ * BC_ERR_INVALID except with probability about 2^-64),
  * d_sources[k], d_out_bc[n] (overwritten with scale * sum_s delta_s, in the
  * caller's vertex ids) and d_status (one int, set to BC_OK, BC_ERR_INVALID or
  * BC_ERR_TIMEOUT when the work completes).  Work is enqueued on `stream`
@@ -343,8 +371,13 @@ int bc_step_destroy(bc_step_t step);
  * The first call on a device looks up the array's device address, so make it
  * before any stream capture.  Calls share the array and each re-initialises
  * it; calls whose work overlaps on the GPU (other streams or threads without
- * ordering) race on it.  Tuning fields of bc_config (bucket_width, settle_in,
- * phase_cap) apply.
+ * ordering) race on it.  On BC_ERR_INVALID no source runs and d_out_bc is all
+ * zeros.  The bc_config fields that apply: bucket_width (0 = a fixed 64: the
+ * call never reads the weights on the host, so it cannot derive the mean
+ * Delta_node that bc_compute uses; pass the graph's own width for high-weight
+ * graphs), settle_in, phase_cap, warp_degree and team_degree.  The team size
+ * follows the average degree (>= 20: 512, >= 12: 256, else 128 threads); the
+ * other fields are ignored.
  */
 #define BC_NOALLOC_SCRATCH_BYTES (64ull << 20)
 int bc_compute_noalloc(const uint64_t *d_row_ptr, const uint32_t *d_col_idx, const uint32_t *d_w, uint32_t n,

@@ -43,6 +43,37 @@ def build(force: bool = False, extra_flags=(), out_path: str | None = None) -> s
     return out
 
 
+_TIMING_LIB = None
+TIMING_FLAGS: tuple = ()
+
+
+def timing_lib():
+    """A second build of the same brandes.c, with the optimisation flags of a
+    CPU baseline (-O3 and the host's own instruction set: -mcpu=native on
+    aarch64, -march=native elsewhere; -O3 alone if the compiler rejects
+    that).  Only timed, never used for parity: the tests use the pinned
+    portable -O2 build.  Returns the bound library; TIMING_FLAGS says what it
+    was built with."""
+    global _TIMING_LIB, TIMING_FLAGS
+    if _TIMING_LIB is None:
+        import platform
+
+        native = "-mcpu=native" if platform.machine().lower() in ("aarch64", "arm64") else "-march=native"
+        out = os.path.join(_BUILD, "liboracle_timing.so")
+        for flags in (("-O3", native), ("-O3",)):
+            try:
+                build(force=True, extra_flags=flags, out_path=out)
+            except subprocess.CalledProcessError:
+                continue
+            TIMING_FLAGS = flags
+            _TIMING_LIB = load(out)
+            break
+        else:
+            TIMING_FLAGS = ("-O2",)
+            _TIMING_LIB = load()
+    return _TIMING_LIB
+
+
 def _bind(lib):
     lib.oracle_sssp.argtypes = [ctypes.c_uint32, _u64p, _u32p, _u32p, ctypes.c_uint32, _u64p, _f64p, _u32p, _u32p]
     lib.oracle_delta.argtypes = [ctypes.c_uint32, _u64p, _u32p, _u32p, ctypes.c_uint32, _f64p]

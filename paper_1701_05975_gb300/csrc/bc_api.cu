@@ -535,6 +535,8 @@ void record_stats(bc_graph* g, const Ctl& c, const RunCfg& r, uint32_t slots) {
   g->last.team_threads = r.team;
   g->last.slots = slots;
   g->last.bucket_width = r.width;
+  g->last.warp_degree = r.warp_deg;
+  g->last.team_degree = r.team_deg;
 }
 
 int check_graph(bc_graph_t g) {
@@ -620,6 +622,71 @@ int compute_plain(bc_graph* g, const uint32_t* sources, uint32_t k, double scale
   return status_from_dev(dev);
 }
 
+// 64-bit finaliser of SplitMix64 (Steele, Lea and Flood, OOPSLA 2014).
+uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+// True when the multiset of entries (v -> u, w) equals that of their reverses
+// (u -> v, w), compared through a sum mod 2^64 of a hash of each entry: exact
+// for a symmetric CSR, and an asymmetric one passes only with probability about
+// 2^-64.  O(nnz).
+bool symmetric_by_hash(uint32_t n, const uint64_t* rp, const uint32_t* col, const uint32_t* w) {
+  uint64_t fwd = 0, rev = 0;
+  for (uint32_t v = 0; v < n; ++v)
+    for (uint64_t e = rp[v]; e < rp[v + 1]; ++e) {
+      const uint64_t hw = mix64((uint64_t)w[e] + 0x9e3779b97f4a7c15ull);
+      fwd += mix64((((uint64_t)v << 32) | col[e]) ^ hw);
+      rev += mix64((((uint64_t)col[e] << 32) | v) ^ hw);
+    }
+  return fwd == rev;
+}
+
+// Upper bound on every finite shortest-path distance of a symmetric graph:
+// within a component, two vertices are joined through the vertex r its
+// breadth-first search starts from by a path of at most 2 ecc(r) edges (ecc =
+// hop eccentricity), each of weight at most max_w.  O(n + nnz).
+uint64_t hop_distance_bound(uint32_t n, const uint64_t* rp, const uint32_t* col, uint32_t max_w) {
+  std::vector<uint32_t> hop(n, 0xffffffffu), q(n);
+  uint64_t max_ecc = 0;
+  for (uint32_t r = 0; r < n; ++r) {
+    if (hop[r] != 0xffffffffu) continue;
+    uint32_t head = 0, tail = 0;
+    hop[r] = 0;
+    q[tail++] = r;
+    while (head < tail) {
+      const uint32_t v = q[head++];
+      for (uint64_t e = rp[v]; e < rp[v + 1]; ++e) {
+        const uint32_t u = col[e];
+        if (hop[u] == 0xffffffffu) {
+          hop[u] = hop[v] + 1;
+          q[tail++] = u;
+        }
+      }
+    }
+    max_ecc = std::max<uint64_t>(max_ecc, hop[q[tail - 1]]);
+  }
+  return 2ull * max_ecc * std::max<uint32_t>(max_w, 1);
+}
+
+// Distance word width.  32 bits when every value the kernels form fits with
+// room to spare: a finite distance D, a tentative distance D + w and a
+// threshold key D + 2 max_w stay below half of the 32-bit INF word.  D is
+// bounded by (n - 1) max_w for any graph, and for symmetric undirected graphs
+// also by the hop bound above (the 1024 x 1024 grid with weights up to 10^4:
+// about 5 * 10^7 against 10^10).
+int distance_bits(uint32_t n, const uint64_t* rp, const uint32_t* col, const uint32_t* w, uint32_t max_w,
+                  bool directed) {
+  const uint64_t mw = std::max<uint32_t>(max_w, 1);
+  const uint64_t half = 0x7fffffffull;
+  if ((uint64_t)n * mw + 2 * mw < half) return 32;
+  if (directed || !symmetric_by_hash(n, rp, col, w)) return 64;
+  const uint64_t bound = hop_distance_bound(n, rp, col, max_w);
+  return bound + 2 * mw < half ? 32 : 64;
+}
+
 std::string fingerprint(uint32_t n, uint64_t nnz, const uint64_t* rp, const uint32_t* col, const uint32_t* w) {
   uint64_t h = 1469598103934665603ull;
   auto mix = [&](uint64_t x) {
@@ -649,9 +716,10 @@ int bcgpu::set_error(int code, const char* msg) { return fail(code, "%s", msg); 
 struct bcgpu::ServeLease {
   bc_graph* g;
   Workspace* w;
-  cudaStream_t st;
-  cudaEvent_t ev;
+  cudaStream_t st;   // stream of the latest source batch
+  cudaEvent_t ev;    // recorded after each source batch
   uint32_t k;
+  uint32_t slot_cap;  // slabs the lease holds
 };
 
 int bcgpu::graph_device(const bc_graph* g) { return g->device; }
@@ -672,37 +740,63 @@ int bcgpu::serve_plan(bc_graph* g, ServePlan* out) {
   return BC_OK;
 }
 
-int bcgpu::serve_start(bc_graph* g, const uint32_t* sources, uint32_t k, double scale, uint32_t slots,
-                       cudaStream_t st, ServeLease** out) {
-  RunCfg r = resolve(g);
-  r.mode = BC_MODE_BATCHED;
+int bcgpu::serve_open(bc_graph* g, const uint32_t* sources, uint32_t k, uint32_t slot_cap, cudaStream_t st,
+                      ServeLease** out) {
   Workspace* w = nullptr;
-  int rc = ws_acquire(g, std::max<uint32_t>(slots, 1), k, st, &w);
+  const uint32_t cap = std::max<uint32_t>(slot_cap, 1);
+  int rc = ws_acquire(g, cap, k, st, &w);
   if (rc) return rc;
   cudaError_t e = cudaSuccess;
   if (!w->host_bc) e = cudaMallocHost(&w->host_bc, (size_t)g->n * 8);
+  // the request's sources and its zeroed accumulator, ordered before its first source batch on st
   if (e == cudaSuccess && k) {
     memcpy(w->host_src, sources, (size_t)k * 4);
     e = cudaMemcpyAsync(w->src, w->host_src, (size_t)k * 4, cudaMemcpyHostToDevice, st);
   }
+  if (e == cudaSuccess) e = cudaMemsetAsync(w->bc, 0, (size_t)g->n * 8, st);
+  // the first batch, on whichever stream, waits for this event
+  if (e == cudaSuccess) e = cudaEventRecord(w->done, st);
   if (e != cudaSuccess) {
     ws_release(g, w, st);
-    return cuda_fail(e, "serve_start");
+    return cuda_fail(e, "serve_open");
   }
-  rc = enqueue_batched(g, w, r, w->src, k, scale, w->bc, nullptr, std::min<uint32_t>(std::max<uint32_t>(slots, 1), w->slots),
-                       0, st, false);
-  if (!rc) {
-    e = cudaMemcpyAsync(w->host_ctl, w->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(w->host_bc, w->bc, (size_t)g->n * 8, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaEventRecord(w->done, st);
-    if (e != cudaSuccess) rc = cuda_fail(e, "serve_start");
-  }
-  if (rc) {
-    ws_release(g, w, st);
-    return rc;
-  }
-  *out = new ServeLease{g, w, st, w->done, k};
+  *out = new ServeLease{g, w, st, w->done, k, std::min(cap, w->slots)};
   return BC_OK;
+}
+
+uint32_t bcgpu::serve_slot_cap(const ServeLease* l) { return l->slot_cap; }
+
+int bcgpu::serve_batch(ServeLease* l, uint32_t first, uint32_t count, uint32_t slots, bool last, double scale,
+                       cudaStream_t st) {
+  bc_graph* g = l->g;
+  Workspace* w = l->w;
+  RunCfg r = resolve(g);
+  r.mode = BC_MODE_BATCHED;
+  l->st = st;
+  // the previous batch of this request (possibly on another stream) comes first
+  cudaError_t e = cudaStreamWaitEvent(st, w->done, 0);
+  if (e == cudaSuccess) e = cudaMemsetAsync(w->ctl, 0, sizeof(Ctl), st);
+  const uint32_t sl = std::max<uint32_t>(1, std::min<uint32_t>(slots, l->slot_cap));
+  if (e == cudaSuccess) {
+    BatchArgs a = make_args(g, w, r, w->src + first, count, w->bc, nullptr, sl, 0);
+    e = launch_batched(a, g->dist_bits, (int)r.team, grid_for_slots(r.team, sl), st);
+  }
+  if (e == cudaSuccess && last && scale != 1.0) e = launch_scale(w->bc, g->n, scale, st);
+  if (e == cudaSuccess && last)
+    e = cudaMemcpyAsync(w->host_bc, w->bc, (size_t)g->n * 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(w->host_ctl, w->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st);
+  // recorded even after a failed enqueue, so the workspace is released only
+  // once whatever did get enqueued has run
+  const cudaError_t er = cudaEventRecord(w->done, st);
+  if (e == cudaSuccess) e = er;
+  if (e != cudaSuccess) return cuda_fail(e, "serving batch");
+  return BC_OK;
+}
+
+int bcgpu::serve_batch_status(ServeLease* l) {
+  cudaError_t e = cudaEventSynchronize(l->ev);
+  if (e != cudaSuccess) return cuda_fail(e, "serving batch");
+  return status_from_dev(l->w->host_ctl->err);
 }
 
 bool bcgpu::serve_ready(ServeLease* l) { return cudaEventQuery(l->ev) != cudaErrorNotReady; }
@@ -712,7 +806,7 @@ int bcgpu::serve_finish(ServeLease* l, double* out_bc) {
   int rc = BC_OK;
   if (e != cudaSuccess) {
     rc = cuda_fail(e, "serving run");
-  } else {
+  } else if (out_bc) {
     memcpy(out_bc, l->w->host_bc, (size_t)l->g->n * 8);
     rc = status_from_dev(l->w->host_ctl->err);
   }
@@ -879,7 +973,7 @@ int bc_graph_create(const uint64_t* row_ptr, const uint32_t* col_idx, const uint
     }
     g->width_default = rows ? std::max<uint64_t>(1, (uint64_t)(sum / (double)rows + 0.5)) : 1;
   }
-  g->dist_bits = ((uint64_t)n * std::max<uint32_t>(max_w, 1) * 2ull < 0xffffffffull) ? 32 : 64;
+  g->dist_bits = distance_bits(n, row_ptr, col_idx, w, max_w, directed);
   g->fingerprint = fingerprint(n, nnz, row_ptr, col_idx, w);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -1064,6 +1158,8 @@ int compute_async(bc_graph* g, const uint32_t* d_sources, uint32_t k, double sca
   g->last.team_threads = r.team;
   g->last.slots = slots;
   g->last.bucket_width = r.width;
+  g->last.warp_degree = r.warp_deg;
+  g->last.team_degree = r.team_deg;
   return BC_OK;
 }
 
@@ -1086,7 +1182,7 @@ int bc_sync_status(bc_graph_t g, void* stream) {
   if (int rc = check_graph(g)) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   CK(cudaSetDevice(g->device));
-  CK(cudaStreamSynchronize(st));
+  const cudaError_t se = cudaStreamSynchronize(st);
   Workspace* w = nullptr;
   {
     std::lock_guard<std::mutex> lk(g->mu);
@@ -1095,6 +1191,11 @@ int bc_sync_status(bc_graph_t g, void* stream) {
       w = it->second;
       g->async_ws.erase(it);
     }
+  }
+  if (se != cudaSuccess) {
+    // the stream's work has ended (with an error): its workspace goes back to the pool
+    if (w) ws_release(g, w, st);
+    return cuda_fail(se, "cudaStreamSynchronize");
   }
   if (!w) return BC_OK;
   const Ctl c = *w->host_ctl;  // read before the workspace goes back to the pool
@@ -1260,6 +1361,12 @@ int bc_autotune(bc_graph_t g, const uint32_t* sources, uint32_t k_probe) {
   base.mode = BC_MODE_BATCHED;
   base.settle_in = 1;
   base.algo = (user.algorithm == BC_ALGO_DELTA) ? ALGO_DELTA : ALGO_STRICT;
+  // every candidate starts from the built-in thresholds (not a previous tuning)
+  base.warp_deg = user.warp_degree ? user.warp_degree : 32u;
+  auto team_deg_of = [&](uint32_t team, uint32_t warp_deg) {
+    return std::max(user.team_degree ? user.team_degree : 8u * team, warp_deg);
+  };
+  base.team_deg = team_deg_of(base.team, base.warp_deg);
   double ms = 0;
   if (int rc = timed(base, &ms)) return rc;  // warm-up: workspace allocation
   double best_ms = 1e300;
@@ -1273,6 +1380,7 @@ int bc_autotune(bc_graph_t g, const uint32_t* sources, uint32_t k_probe) {
       RunCfg r = base;
       r.team = team;
       r.width = width;
+      r.team_deg = team_deg_of(team, r.warp_deg);
       if (int rc = timed(r, &ms)) return rc;
       if (ms < best_ms) {
         best_ms = ms;
@@ -1300,6 +1408,7 @@ int bc_autotune(bc_graph_t g, const uint32_t* sources, uint32_t k_probe) {
         r.algo = ALGO_DELTA;
         r.team = team;
         r.width = width;
+        r.team_deg = team_deg_of(team, r.warp_deg);
         if (int rc = timed(r, &ms)) return rc;
         if (ms < best_ms) {
           best_ms = ms;
@@ -1312,12 +1421,49 @@ int bc_autotune(bc_graph_t g, const uint32_t* sources, uint32_t k_probe) {
     }
   }
   if (best.team == 0) return fail(BC_ERR_INVALID, "autotune: the configuration pins every candidate out");
+  // degree thresholds of the strict schedule's expansion tiers: first the
+  // warp threshold, then the team threshold (as a multiple of the team size)
+  if (best.algo == BC_ALGO_STRICT) {
+    RunCfg r = base;
+    r.team = best.team;
+    r.width = best.width;
+    if (!user.warp_degree) {
+      uint32_t best_wd = r.warp_deg;
+      for (uint32_t wd : {8u, 16u, 32u, 64u}) {
+        if (wd == r.warp_deg) continue;  // the built-in value was timed with the team and width above
+        r.warp_deg = wd;
+        r.team_deg = team_deg_of(r.team, wd);
+        if (int rc = timed(r, &ms)) return rc;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best_wd = wd;
+        }
+      }
+      r.warp_deg = best_wd;
+      r.team_deg = team_deg_of(r.team, best_wd);
+      best.warp_deg = best_wd;
+    }
+    if (!user.team_degree) {
+      uint32_t best_td = 0;
+      for (uint32_t mult : {2u, 32u}) {
+        r.team_deg = std::max(mult * r.team, r.warp_deg);
+        if (int rc = timed(r, &ms)) return rc;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best_td = r.team_deg;
+        }
+      }
+      if (best_td) best.team_deg = best_td;
+    }
+  }
   // sources in flight: the full resident capacity, or half of it
   if (!user.max_slots) {
     RunCfg r = base;
     r.team = best.team;
     r.width = best.width;
     r.algo = best.algo == BC_ALGO_DELTA ? ALGO_DELTA : ALGO_STRICT;
+    if (best.warp_deg) r.warp_deg = best.warp_deg;
+    r.team_deg = best.team_deg ? best.team_deg : team_deg_of(r.team, r.warp_deg);
     uint32_t full = 0;
     if (int rc = plan_slots(g, r, k_probe, &full)) return rc;
     r.max_slots = std::max<uint32_t>(1, full / 2);

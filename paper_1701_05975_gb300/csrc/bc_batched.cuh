@@ -128,6 +128,10 @@ struct TeamShared {
   uint32_t near_len, far_len, far2_len, S_len, nlev;
   uint32_t pair_len, pair_over;
   int stop;
+  // strict schedule: per-section SM cycles and queue entries scanned (kept by
+  // the team leader in shared memory, out of every thread's registers)
+  unsigned long long cyc_expand, cyc_refill, cyc_settle, cyc_back, near_sc, far_sc;
+  long long tmark;
   D split, split2;  // near < split <= far < split2 <= far2
   uint32_t off[TEAM + 1];
   uint32_t vtx[TEAM];
@@ -788,15 +792,22 @@ __device__ __forceinline__ void push_level_pairs_edges(const uint2* pairs, const
   }
 }
 
+// Team leader: add the cycles since the last mark to a section counter.
+template <typename D, int TEAM>
+__device__ __forceinline__ void lap(TeamShared<D, TEAM>& sh, int t, unsigned long long& section) {
+  if (t == 0) {
+    const long long now = clock64();
+    section += (unsigned long long)(now - sh.tmark);
+    sh.tmark = now;
+  }
+}
+
 // Returns false when the source hit the phase cap (its slab is then dirty).
 template <typename D, int TEAM, bool PACKED>
 __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, TEAM>& sh, uint32_t s, int t) {
   const D INF = dinf<D>();
   unsigned long long relax = 0, scanned = 0;
   uint64_t phases = 0, refills = 0;
-  // per-section cycle counters (read by the team leader only)
-  unsigned long long cyc_expand = 0, cyc_refill = 0, cyc_settle = 0, cyc_back = 0, near_sc = 0, far_sc = 0;
-  long long c0 = clock64();
   // Algorithm 1 / 4: d = INF everywhere already (slab invariant)
   if (t == 0) {
     sl.d[s] = 0;
@@ -815,6 +826,7 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
     sh.split = sat_add<D>((D)0, a.width);
     sh.split2 = sat_add<D>((D)0, far_span(a.width));
     sh.staged = 0;
+    sh.cyc_expand = sh.cyc_refill = sh.cyc_settle = sh.cyc_back = sh.near_sc = sh.far_sc = 0;
   }
   team_sync<TEAM>();
   uint32_t f0 = 0, f1 = 1;
@@ -823,7 +835,7 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
   const bool stage = BCGPU_STAGE && a.g.in_row_ptr == nullptr;
   for (;;) {
     const D split0 = sh.split;
-    c0 = clock64();
+    if (t == 0) sh.tmark = clock64();
     if (a.g.in_row_ptr) {
       // directed: sigma from in-edges, then relax out-edges
       expand_forward<D, TEAM, PACKED, WALK_PULL>(a, in_rows(a.g), sl, sh, sl.S, f0, f1, s, t, split0, relax,
@@ -836,8 +848,7 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
     }
     // DAG edges into the batch just expanded end here
     if (t == 0) sl.pend[sh.nlev - 1] = sh.pair_len;
-    cyc_expand += clock64() - c0;
-    c0 = clock64();
+    lap(sh, t, sh.cyc_expand);
     // refill the near queue from the far queue when it runs dry, and the far
     // queue from the second far level when that runs dry too
     while (sh.near_len == 0 && (sh.far_len > 0 || sh.far2_len > 0)) {
@@ -845,7 +856,7 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
         // every vertex below split2 is settled: split moves up to split2
         const D old2 = sh.split2;
         const uint32_t fl2 = sh.far2_len;
-        far_sc += 2ull * fl2;
+        if (t == 0) sh.far_sc += 2ull * fl2;
         D lo = INF, dummy = INF;
         for (uint32_t base = 0; base < fl2; base += TEAM) {
           const uint32_t j = base + t;
@@ -887,7 +898,7 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
       const D old = sh.split;
       const D cap = sh.split2;
       const uint32_t fl = sh.far_len;
-      far_sc += 2ull * fl;
+      if (t == 0) sh.far_sc += 2ull * fl;
       D lo = INF, dummy = INF;
       for (uint32_t base = 0; base < fl; base += TEAM) {
         const uint32_t j = base + t;
@@ -925,12 +936,11 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
         sh.split = ns;
       }
       ++refills;
-      if (phases + refills > a.phase_cap && t == 0) sh.stop = 1;
+      if (phases + refills > a.phase_cap && t == 0) sh.stop = DEV_ERR_TIMEOUT;
       team_sync<TEAM>();
       if (sh.stop) break;
     }
-    cyc_refill += clock64() - c0;
-    c0 = clock64();
+    lap(sh, t, sh.cyc_refill);
     if (sh.stop || sh.near_len == 0) break;
     // threshold: Delta' = min(min_near (D + Delta_node), split) <= Delta_i
     const uint32_t nl = sh.near_len;
@@ -941,7 +951,7 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
     if (nl <= TEAM * NEAR_REGS) {
       staged_now = stage;
       // the whole near queue fits in registers: one gather pass
-      near_sc += nl;
+      if (t == 0) sh.near_sc += nl;
       uint32_t uu[NEAR_REGS];
       D dd[NEAR_REGS], dn[NEAR_REGS], dni[NEAR_REGS];
       D out = INF, dm = INF;
@@ -995,7 +1005,7 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
         kept += min((uint32_t)TEAM, nl - base) - stot;
       }
     } else {
-      near_sc += 2ull * nl;
+      if (t == 0) sh.near_sc += 2ull * nl;
       D out = INF, dm = INF;
       for (uint32_t base = 0; base < nl; base += TEAM) {
         const uint32_t j = base + t;
@@ -1035,19 +1045,27 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
       sh.near_len = kept;
       sh.S_len = S0 + nset;
       sh.staged = staged_now ? min(nset, (uint32_t)TEAM) : 0u;
-      sh.nlev += 1;
-      sl.ends[sh.nlev] = S0 + nset;
-      if (phases + refills > a.phase_cap) sh.stop = 1;
+      if (nset == 0) {
+        // every phase settles the smallest candidate (its d is below both
+        // d + Delta_node and the split); a phase that settles nothing means
+        // an input outside the contract (an asymmetric "undirected" CSR):
+        // stop before the level arrays could outgrow n + 2 entries
+        sh.stop = DEV_ERR_INTERNAL;
+      } else {
+        sh.nlev += 1;
+        sl.ends[sh.nlev] = S0 + nset;
+        if (phases + refills > a.phase_cap) sh.stop = DEV_ERR_TIMEOUT;
+      }
     }
+    lap(sh, t, sh.cyc_settle);
     team_sync<TEAM>();
-    cyc_settle += clock64() - c0;
     if (sh.stop) break;
     f0 = S0;
     f1 = S0 + nset;
   }
   const bool failed = sh.stop != 0;
   if (failed) {
-    if (t == 0) atomicCAS(a.err, DEV_OK, DEV_ERR_TIMEOUT);
+    if (t == 0) atomicCAS(a.err, DEV_OK, sh.stop);
     // every touched vertex is settled (S), near or far: restore d = INF there
     const uint32_t sl_n = sh.S_len, nl_n = sh.near_len, fl_n = sh.far_len, fl2_n = sh.far2_len;
     for (uint32_t j = t; j < sl_n; j += TEAM) sl.d[ldcg(&sl.S[j])] = INF;
@@ -1061,7 +1079,7 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
     }
   } else {
     const uint32_t nlev = sh.nlev;
-    c0 = clock64();
+    if (t == 0) sh.tmark = clock64();
     if ((!a.ebc || sl.pair_e) && !sh.pair_over) {
       // Algorithm 3 over the recorded DAG edges: levels in reverse; finalize
       // the level's vertices, then push their coefficients to predecessors
@@ -1086,7 +1104,7 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
         accumulate_level<D, TEAM, PACKED>(a, sl, sh, sl.S, b0, b1, s, t, scanned);
       }
     }
-    cyc_back += clock64() - c0;
+    lap(sh, t, sh.cyc_back);
     // restore the slab invariant: d = INF on every vertex this source reached
     const uint32_t n_reached = sh.S_len;
     for (uint32_t j = t; j < n_reached; j += TEAM) sl.d[ldcg(&sl.S[j])] = INF;
@@ -1110,12 +1128,12 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
       atomicAdd(&a.stats[STAT_DAG_EDGES], (unsigned long long)sh.pair_len);
       atomicAdd(&a.stats[STAT_LEVELS], (unsigned long long)sh.nlev);
       atomicAdd(&a.stats[STAT_PAIR_OVERFLOW], (unsigned long long)sh.pair_over);
-      atomicAdd(&a.stats[STAT_CYC_EXPAND], cyc_expand);
-      atomicAdd(&a.stats[STAT_CYC_REFILL], cyc_refill);
-      atomicAdd(&a.stats[STAT_CYC_SETTLE], cyc_settle);
-      atomicAdd(&a.stats[STAT_CYC_BACKWARD], cyc_back);
-      atomicAdd(&a.stats[STAT_NEAR_SCANNED], near_sc);
-      atomicAdd(&a.stats[STAT_FAR_SCANNED], far_sc);
+      atomicAdd(&a.stats[STAT_CYC_EXPAND], sh.cyc_expand);
+      atomicAdd(&a.stats[STAT_CYC_REFILL], sh.cyc_refill);
+      atomicAdd(&a.stats[STAT_CYC_SETTLE], sh.cyc_settle);
+      atomicAdd(&a.stats[STAT_CYC_BACKWARD], sh.cyc_back);
+      atomicAdd(&a.stats[STAT_NEAR_SCANNED], sh.near_sc);
+      atomicAdd(&a.stats[STAT_FAR_SCANNED], sh.far_sc);
     }
   }
   team_sync<TEAM>();
@@ -1318,10 +1336,22 @@ __device__ bool run_source_ds(const BatchArgs& a, const Slab<D>& sl, TeamShared<
   return err == DEV_OK;
 }
 
+// Resident CTAs per SM that a CTA team's register budget is compiled for:
+// 64 registers per thread (2048 threads per SM for 32-bit distances; 7/8 of
+// that for 64-bit ones, where 64 registers would spill).  Measured with
+// -Xptxas -v: naming only the block size let the compiler settle on 56-64
+// registers with 24-536 bytes of spills per thread in every CTA-team variant;
+// with the residency stated, the 32-bit variants up to 512 threads use 64
+// registers and no spills.  Warp teams keep the compiler's choice.
+template <typename D, int TEAM, int BLOCK>
+__host__ __device__ constexpr int min_blocks_of() {
+  return TEAM == 32 ? 1 : (sizeof(D) == 4 ? 1024 / BLOCK : (BLOCK <= 256 ? 896 / BLOCK : 1024 / BLOCK));
+}
+
 // One instantiation per schedule, so the strict schedule's register allocation
 // does not pay for the delta-stepping code.
 template <typename D, int TEAM, int BLOCK, bool PACKED, int ALGO>
-__global__ void __launch_bounds__(BLOCK) bc_batched_kernel(const BatchArgs a) {
+__global__ void __launch_bounds__(BLOCK, (min_blocks_of<D, TEAM, BLOCK>())) bc_batched_kernel(const BatchArgs a) {
   static_assert(TEAM == 32 || TEAM == BLOCK, "a CTA holds either warp teams or one team");
   constexpr int NTEAMS = BLOCK / TEAM;
   __shared__ TeamShared<D, TEAM> shared_teams[NTEAMS];

@@ -163,8 +163,13 @@ struct bc_graph;
 namespace bcgpu {
 
 // Serving support (implemented in bc_api.cu, used by the scheduler in
-// bc_serve.cu).  A lease is one request's run on one stream: its workspace
-// stays reserved until serve_finish copies the result out.
+// bc_serve.cu).  A lease is one request's workspace (slabs, source list,
+// device accumulator), held from serve_open to serve_finish; the request's
+// sources run as a sequence of source batches (serve_batch), each one
+// persistent launch that adds into the accumulator, on whichever stream the
+// scheduler picks.  The last batch also scales the sum and copies it to
+// pinned host memory; serve_finish hands it to the caller and releases the
+// workspace.
 struct ServeLease;
 struct ServePlan {
   uint32_t team;        // threads per source
@@ -173,10 +178,17 @@ struct ServePlan {
   uint64_t fixed_bytes; // per-request device bytes besides the slabs
 };
 int serve_plan(bc_graph* g, ServePlan* out);
-int serve_start(bc_graph* g, const uint32_t* sources, uint32_t k, double scale, uint32_t slots, cudaStream_t st,
-                ServeLease** out);
-bool serve_ready(ServeLease* l);
-int serve_finish(ServeLease* l, double* out_bc);  // releases the lease
+// Reserve a workspace of up to slot_cap slabs and stage the sources (on st).
+int serve_open(bc_graph* g, const uint32_t* sources, uint32_t k, uint32_t slot_cap, cudaStream_t st,
+               ServeLease** out);
+uint32_t serve_slot_cap(const ServeLease* l);  // slabs actually held
+// Enqueue sources [first, first + count) with `slots` of them in flight; the
+// last batch also applies `scale` and stages the result for serve_finish.
+int serve_batch(ServeLease* l, uint32_t first, uint32_t count, uint32_t slots, bool last, double scale,
+                cudaStream_t st);
+bool serve_ready(ServeLease* l);         // the latest batch has completed
+int serve_batch_status(ServeLease* l);   // its device status (waits for it)
+int serve_finish(ServeLease* l, double* out_bc);  // out_bc may be null (failed request); releases the lease
 int graph_device(const bc_graph* g);
 uint32_t graph_n(const bc_graph* g);
 uint64_t graph_nnz(const bc_graph* g);

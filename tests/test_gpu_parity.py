@@ -371,6 +371,59 @@ def test_wide_weights_use_unpacked_entries_and_64bit_distances():
             assert np.array_equal(d, d_ref) and np.array_equal(sg, sg_ref)
 
 
+def broom_graph(seed):
+    """A 400-vertex star (hub 0) with chords, plus a 100-vertex path hanging
+    off leaf 399; weights 10^6 x U{4..10}.  n x max_w is above 2^31, but the
+    hop eccentricity from the hub is 101, so every distance (up to ~10^9) is
+    bounded by 2 x 101 x 10^7 and fits a 32-bit word."""
+    rng = np.random.default_rng(seed)
+    edges = [(0, i) for i in range(1, 400)] + [(i, i + 1) for i in range(399, 499)]
+    chords = rng.integers(1, 400, size=(300, 2))
+    edges += [(int(a), int(b)) for a, b in chords if a != b]
+    u, v = np.array(edges).T
+    uniq = gen._dedup_pairs(u, v, 500)
+    w = 1_000_000 * rng.integers(4, 11, size=len(uniq[0]))
+    return gen.csr_from_undirected(500, uniq[0], uniq[1], w)
+
+
+@pytest.mark.parametrize("team", [32, 256, 1024])
+def test_hop_bound_gives_32bit_distances_up_to_1e9(team):
+    bc.bc_set_config(team_threads=team)
+    g = broom_graph(61)
+    src = np.arange(g.n, dtype=np.uint32)
+    with bc.Graph(g) as G:
+        assert G.info().dist_bits == 32
+        assert_bc_close(G.compute(src, 1.0), oracle.bc(g, src, 1.0))
+        for s in (0, 250, 499):
+            d, sg, _ = G.sssp_debug(s)
+            d_ref, sg_ref, _ = oracle.sssp(g, s)
+            assert np.array_equal(d, d_ref) and np.array_equal(sg, sg_ref)
+        assert d_ref.max() > 5e8  # the words really hold large distances
+
+
+def test_distance_width_falls_back_to_64_bits():
+    # a long path: the hop bound (2 x 299 x 10^7) does not fit
+    n = 300
+    path = graph(n, [(i, i + 1, 10_000_000) for i in range(n - 1)])
+    with bc.Graph(path) as G:
+        assert G.info().dist_bits == 64
+        src = np.arange(0, n, 3, dtype=np.uint32)
+        assert_bc_close(G.compute(src, 1.0), oracle.bc(path, src, 1.0))
+    # directed graphs keep the (n - 1) max_w bound
+    rng = np.random.default_rng(62)
+    dg = gen.random_small_digraph(400, 0.02, 4_000_000, 10_000_000, rng)
+    with bc.Graph(dg, flags=bc.BC_DIRECTED) as G:
+        assert G.info().dist_bits == 64
+    # an asymmetric CSR passed as undirected: the hop bound does not apply
+    # (the graph is only created, not run: it is outside the undirected contract)
+    b = broom_graph(63)
+    w = b.w.copy()
+    w[0] += 1
+    asym = gen.CSRGraph(n=b.n, row_ptr=b.row_ptr, col=b.col, w=w, name="asym")
+    with bc.Graph(asym) as G:
+        assert G.info().dist_bits == 64
+
+
 @pytest.mark.parametrize("cfg", CONFIGS, ids=lambda c: f"team{c['team_threads']}-in{c['settle_in']}")
 def test_directed_small_graphs(cfg):
     bc.bc_set_config(**cfg)
