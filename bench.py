@@ -555,6 +555,8 @@ def main():
     ap.add_argument("--max-slots", type=int, default=0, help="cap on sources in flight (0 = automatic)")
     ap.add_argument("--team", type=int, default=0, help="threads per source (0 = automatic / autotuned)")
     ap.add_argument("--width", type=int, default=0, help="near/far split width (0 = automatic / autotuned)")
+    ap.add_argument("--algorithm", type=int, default=0, help="per-source schedule: 0 = automatic / autotuned, "
+                    "1 = strict, 2 = delta-stepping")
     ap.add_argument("--clocks-csv", default="", help="also keep the raw nvidia-smi clock samples at this path "
                     "({rank} is replaced by the rank)")
     ap.add_argument("--no-graph", action="store_true", help="enqueue each step with bc_compute_async instead of "
@@ -608,8 +610,8 @@ def main():
         bc.bc_set_config(team_threads=args.team)
     if args.width:
         bc.bc_set_config(bucket_width=args.width)
-    if opts.get("algorithm"):
-        bc.bc_set_config(algorithm=opts["algorithm"])
+    if opts.get("algorithm") or args.algorithm:
+        bc.bc_set_config(algorithm=args.algorithm or opts["algorithm"])
     t0 = time.perf_counter()
     G = bc.Graph(g, flags=bc.BC_DIRECTED if opts.get("directed") else 0)
     prep_s = time.perf_counter() - t0  # graph prep: validation, relabeling, upload, packing, Delta_node
