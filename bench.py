@@ -557,6 +557,12 @@ def main():
     ap.add_argument("--width", type=int, default=0, help="near/far split width (0 = automatic / autotuned)")
     ap.add_argument("--algorithm", type=int, default=0, help="per-source schedule: 0 = automatic / autotuned, "
                     "1 = strict, 2 = delta-stepping")
+    ap.add_argument("--warp-degree", type=int, default=0, help="rows with at least this many entries get a warp "
+                    "(0 = automatic / autotuned)")
+    ap.add_argument("--team-degree", type=int, default=0, help="rows with at least this many entries get the whole "
+                    "team (0 = automatic / autotuned)")
+    ap.add_argument("--settle-in", type=int, default=0, help="settle test: 1 = OUT or IN with the settled-neighbour "
+                    "bound, 2 = OUT, 3 = OUT or IN (0 = automatic / autotuned)")
     ap.add_argument("--clocks-csv", default="", help="also keep the raw nvidia-smi clock samples at this path "
                     "({rank} is replaced by the rank)")
     ap.add_argument("--no-graph", action="store_true", help="enqueue each step with bc_compute_async instead of "
@@ -612,6 +618,10 @@ def main():
         bc.bc_set_config(bucket_width=args.width)
     if opts.get("algorithm") or args.algorithm:
         bc.bc_set_config(algorithm=args.algorithm or opts["algorithm"])
+    if args.warp_degree or args.team_degree:
+        bc.bc_set_config(warp_degree=args.warp_degree, team_degree=args.team_degree)
+    if args.settle_in:
+        bc.bc_set_config(settle_in=args.settle_in)
     t0 = time.perf_counter()
     G = bc.Graph(g, flags=bc.BC_DIRECTED if opts.get("directed") else 0)
     prep_s = time.perf_counter() - t0  # graph prep: validation, relabeling, upload, packing, Delta_node
@@ -710,7 +720,10 @@ def main():
                          % (G.info().device_bytes / 1e6, int(st.slots), G.info().slab_bytes / 1e6),
                    "team_threads": int(st.team_threads), "slots": int(st.slots),
                    "bucket_width": int(st.bucket_width), "warp_degree": int(st.warp_degree),
-                   "team_degree": int(st.team_degree), "parallelism": f"replicas x{ws}",
+                   "team_degree": int(st.team_degree),
+                   "settle_test": {1: "OUT or IN, settled-neighbour bound", 2: "OUT (Eq. 2 + Eq. 4)",
+                                   3: "OUT or IN"}.get(int(st.settle_in), "n/a"),
+                   "parallelism": f"replicas x{ws}",
                    "autotune": {"probe_sources": probe, "seconds": round(tune_s, 2)},
                    "graph_prep_s": round(prep_s, 3),
                    "launch": "CUDA graph (bc_step_launch)" if use_graph else (
@@ -730,6 +743,8 @@ def main():
         "run_stats": {"phases_per_source": st.phases / max(st.sources, 1),
                       "refills_per_source": st.refills / max(st.sources, 1),
                       "reached_per_source": st.reached / max(st.sources, 1),
+                      "near_entries_scanned_per_source": st.near_scanned / max(st.sources, 1),
+                      "far_entries_scanned_per_source": st.far_scanned / max(st.sources, 1),
                       # share of each source's SM cycles (team leader's clock) per section
                       "cycle_shares": cycle_shares(st)},
     }

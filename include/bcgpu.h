@@ -96,7 +96,11 @@ typedef struct bc_config {
                              else by entries walked per vertex (>= 20: 1024 or 512, >= 6: 256, else 128) */
   uint32_t max_slots;     /* cap on sources in flight at once (per-source slabs held in device memory) */
   uint32_t settle_in;     /* 1: settle by the strict OUT criterion (Eq. 2 + Eq. 4) OR the strict IN
-                             criterion; 2: OUT only (the paper's criterion alone); 0 = automatic (1) */
+                             criterion, each with Delta_node raised to the second smallest incident
+                             weight once the vertex's lightest neighbour is known to be settled
+                             (undirected graphs; a legal refinement, larger batches); 2: OUT only with
+                             Delta_node (the paper's criterion alone); 3: OUT or IN with Delta_node;
+                             0 = automatic (tuned, else 3) */
   uint64_t bucket_width;  /* near/far split width, in distance units (>= 1); 0 = tuned value, else the
                              mean over non-empty rows of the row's smallest weight (Delta_node) */
   uint64_t phase_cap;     /* device cap on phases + queue refills per source; hitting it returns BC_ERR_TIMEOUT.
@@ -301,6 +305,7 @@ typedef struct bc_run_stats {
   uint32_t algorithm;       /* schedule of the run: BC_ALGO_STRICT or BC_ALGO_DELTA */
   uint32_t warp_degree;     /* degree thresholds of the run's forward expansion: rows with at least */
   uint32_t team_degree;     /* warp_degree entries got a warp each, with at least team_degree the whole team */
+  uint32_t settle_in;       /* settle test of the run (bc_config.settle_in values 1, 2 or 3) */
 } bc_run_stats;
 
 int bc_last_run_stats(bc_graph_t g, bc_run_stats *out);

@@ -67,7 +67,8 @@ class bc_run_stats(ctypes.Structure):
                 ("cycles_refill", ctypes.c_uint64), ("cycles_settle", ctypes.c_uint64),
                 ("cycles_backward", ctypes.c_uint64), ("near_scanned", ctypes.c_uint64),
                 ("far_scanned", ctypes.c_uint64), ("levels", ctypes.c_uint64), ("algorithm", ctypes.c_uint32),
-                ("warp_degree", ctypes.c_uint32), ("team_degree", ctypes.c_uint32)]
+                ("warp_degree", ctypes.c_uint32), ("team_degree", ctypes.c_uint32),
+                ("settle_in", ctypes.c_uint32)]
 
 
 class bc_serving_stats(ctypes.Structure):

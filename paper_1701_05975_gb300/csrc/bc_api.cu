@@ -151,6 +151,8 @@ struct bc_graph {
   uint32_t* adjp = nullptr;  // packed 32-bit entries when neighbour and weight fit
   uint32_t col_bits = 0;
   uint32_t* dnode = nullptr;
+  uint32_t* dnode2 = nullptr;     // undirected graphs: second smallest incident weight
+  uint32_t* dnode_arg = nullptr;  // ... and the neighbour of the smallest
   double* ebc = nullptr;  // lazily allocated [nnz]
   bool relabeled = false;
   bool directed = false;
@@ -189,6 +191,8 @@ GraphDev view(const bc_graph* g) {
   v.adjp = g->adjp;
   v.col_bits = g->col_bits;
   v.dnode = g->dnode;
+  v.dnode2 = g->dnode2;
+  v.dnode_arg = g->dnode_arg;
   v.o2n = g->o2n;
   v.n2o = g->n2o;
   v.e2o = g->e2o;
@@ -222,6 +226,7 @@ struct RunCfg {
   uint32_t team;
   uint64_t width;
   uint32_t settle_in;
+  uint32_t refine;  // settled-neighbour refinement of Delta_node (undirected graphs)
   uint64_t phase_cap;
   uint32_t max_slots;
   double mem_fraction;
@@ -248,8 +253,12 @@ RunCfg resolve(const bc_graph* g) {
   if (r.team == 1024 && g->dist_bits != 32) r.team = 512;  // 1024-thread teams hold 32-bit distances only
   r.width = c.bucket_width ? c.bucket_width
                            : (g->tuned.width ? g->tuned.width : g->width_default);
-  uint32_t si = c.settle_in ? c.settle_in : (g->tuned.settle_in ? g->tuned.settle_in : 1u);
-  r.settle_in = (si == 1u) ? 1u : 0u;
+  // 1: OUT or IN with the settled-neighbour refinement; 2: OUT alone with
+  // Delta_node (the paper's test); 3: OUT or IN with Delta_node (the default
+  // until the autotuner has timed the refinement for this graph)
+  uint32_t si = c.settle_in ? c.settle_in : (g->tuned.settle_in ? g->tuned.settle_in : 3u);
+  r.settle_in = (si == 1u || si == 3u) ? 1u : 0u;
+  r.refine = (si == 1u && g->dnode2 != nullptr) ? 1u : 0u;
   // phases <= n (each settles at least the smallest candidate), refills that
   // move entries <= n per queue level, empty refills <= second-level refills + 2:
   // phases + refills <= 4n + 2 (delta-stepping rounds + advances <= 3n)
@@ -472,6 +481,7 @@ BatchArgs make_args(bc_graph* g, Workspace* w, const RunCfg& r, const uint32_t* 
   a.nslots = slots;
   a.width = r.width;
   a.settle_in = r.settle_in;
+  a.refine = r.refine;
   a.phase_cap = r.phase_cap;
   a.err = &w->ctl->err;
   a.stats = w->ctl->stats;
@@ -537,6 +547,7 @@ void record_stats(bc_graph* g, const Ctl& c, const RunCfg& r, uint32_t slots) {
   g->last.bucket_width = r.width;
   g->last.warp_degree = r.warp_deg;
   g->last.team_degree = r.team_deg;
+  g->last.settle_in = r.settle_in ? (r.refine ? 1u : 3u) : 2u;
 }
 
 int check_graph(bc_graph_t g) {
@@ -836,7 +847,7 @@ int bc_set_config(const bc_config* cfg) {
   if (cfg->team_threads && cfg->team_threads != 32 && cfg->team_threads != 128 && cfg->team_threads != 256 &&
       cfg->team_threads != 512 && cfg->team_threads != 1024)
     return fail(BC_ERR_INVALID, "team_threads must be 0, 32, 128, 256, 512 or 1024");
-  if (cfg->settle_in > 2) return fail(BC_ERR_INVALID, "settle_in must be 0, 1 or 2");
+  if (cfg->settle_in > 3) return fail(BC_ERR_INVALID, "settle_in must be 0, 1, 2 or 3");
   if (cfg->algorithm > BC_ALGO_DELTA) return fail(BC_ERR_INVALID, "algorithm must be 0, 1 or 2");
   if (cfg->mem_fraction < 0 || cfg->mem_fraction > 0.95) return fail(BC_ERR_INVALID, "mem_fraction out of range");
   if (cfg->team_degree && cfg->warp_degree && cfg->team_degree < cfg->warp_degree)
@@ -996,6 +1007,10 @@ int bc_graph_create(const uint64_t* row_ptr, const uint32_t* col_idx, const uint
     if (e == cudaSuccess) e = cudaMalloc(&g->adj, std::max<size_t>(nnz, 1) * 8);
   }
   if (e == cudaSuccess) e = cudaMalloc(&g->dnode, (size_t)n * 4);
+  if (!directed) {
+    if (e == cudaSuccess) e = cudaMalloc(&g->dnode2, (size_t)n * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&g->dnode_arg, (size_t)n * 4);
+  }
   if (e == cudaSuccess) e = cudaMalloc(&d_col, std::max<size_t>(nnz, 1) * 4);
   if (e == cudaSuccess) e = cudaMalloc(&d_w, std::max<size_t>(nnz, 1) * 4);
   if (e == cudaSuccess) e = cudaMemcpyAsync(g->row_ptr, row_ptr, ((size_t)n + 1) * 8, cudaMemcpyHostToDevice, g->stream);
@@ -1011,7 +1026,8 @@ int bc_graph_create(const uint64_t* row_ptr, const uint32_t* col_idx, const uint
     if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(g->e2o, e2o.data(), nnz * 4, cudaMemcpyHostToDevice, g->stream);
     g->h_o2n = o2n;
   }
-  if (e == cudaSuccess) e = launch_prep(n, nnz, g->row_ptr, d_col, d_w, g->adj, g->dnode, g->stream);
+  if (e == cudaSuccess)
+    e = launch_prep(n, nnz, g->row_ptr, d_col, d_w, g->adj, g->dnode, g->dnode2, g->dnode_arg, g->stream);
   if (e == cudaSuccess && packed) e = launch_pack32(nnz, d_col, d_w, col_bits, g->adjp, g->stream);
   if (directed && e == cudaSuccess) {
     // same entry form for the in-edge CSR; d_col / d_w are reused for it
@@ -1026,7 +1042,8 @@ int bc_graph_create(const uint64_t* row_ptr, const uint32_t* col_idx, const uint
     if (e == cudaSuccess) e = cudaMemcpyAsync(g->in_row_ptr, irp.data(), ((size_t)n + 1) * 8, cudaMemcpyHostToDevice, g->stream);
     if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(d_col, icol.data(), nnz * 4, cudaMemcpyHostToDevice, g->stream);
     if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(d_w, iw.data(), nnz * 4, cudaMemcpyHostToDevice, g->stream);
-    if (e == cudaSuccess) e = launch_prep(n, nnz, g->in_row_ptr, d_col, d_w, g->in_adj, g->dnode_in, g->stream);
+    if (e == cudaSuccess)
+      e = launch_prep(n, nnz, g->in_row_ptr, d_col, d_w, g->in_adj, g->dnode_in, nullptr, nullptr, g->stream);
     if (e == cudaSuccess && packed) e = launch_pack32(nnz, d_col, d_w, col_bits, g->in_adjp, g->stream);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
@@ -1037,6 +1054,8 @@ int bc_graph_create(const uint64_t* row_ptr, const uint32_t* col_idx, const uint
     cudaFree(g->adj);
     cudaFree(g->adjp);
     cudaFree(g->dnode);
+    cudaFree(g->dnode2);
+    cudaFree(g->dnode_arg);
     cudaFree(g->o2n);
     cudaFree(g->n2o);
     cudaFree(g->e2o);
@@ -1048,7 +1067,7 @@ int bc_graph_create(const uint64_t* row_ptr, const uint32_t* col_idx, const uint
     return cuda_fail(e, "bc_graph_create upload");
   }
   g->device_bytes = (((uint64_t)n + 1) * 8 + nnz * (packed ? 4 : 8) + (uint64_t)n * 4) * (directed ? 2 : 1) +
-                    (relabel ? 8ull * n + 4ull * nnz : 0);
+                    (directed ? 0 : 8ull * n) + (relabel ? 8ull * n + 4ull * nnz : 0);
   *out = g.release();
   return BC_OK;
 }
@@ -1070,6 +1089,8 @@ int bc_graph_destroy(bc_graph_t g) {
   cudaFree(g->adj);
   cudaFree(g->adjp);
   cudaFree(g->dnode);
+  cudaFree(g->dnode2);
+  cudaFree(g->dnode_arg);
   cudaFree(g->ebc);
   cudaFree(g->o2n);
   cudaFree(g->n2o);
@@ -1160,6 +1181,7 @@ int compute_async(bc_graph* g, const uint32_t* d_sources, uint32_t k, double sca
   g->last.bucket_width = r.width;
   g->last.warp_degree = r.warp_deg;
   g->last.team_degree = r.team_deg;
+  g->last.settle_in = r.settle_in ? (r.refine ? 1u : 3u) : 2u;
   return BC_OK;
 }
 
@@ -1360,6 +1382,7 @@ int bc_autotune(bc_graph_t g, const uint32_t* sources, uint32_t k_probe) {
   RunCfg base = resolve(g);
   base.mode = BC_MODE_BATCHED;
   base.settle_in = 1;
+  base.refine = (g->dnode2 && user.settle_in == 1) ? 1u : 0u;
   base.algo = (user.algorithm == BC_ALGO_DELTA) ? ALGO_DELTA : ALGO_STRICT;
   // every candidate starts from the built-in thresholds (not a previous tuning)
   base.warp_deg = user.warp_degree ? user.warp_degree : 32u;
@@ -1386,7 +1409,7 @@ int bc_autotune(bc_graph_t g, const uint32_t* sources, uint32_t k_probe) {
         best_ms = ms;
         best.team = team;
         best.width = width;
-        best.settle_in = 1;
+        best.settle_in = 3;
         best.algo = BC_ALGO_STRICT;
         std::lock_guard<std::mutex> lk(g->mu);
         best_phases = g->last.sources ? (double)g->last.phases / (double)g->last.sources : 0.0;
@@ -1414,7 +1437,7 @@ int bc_autotune(bc_graph_t g, const uint32_t* sources, uint32_t k_probe) {
           best_ms = ms;
           best.team = team;
           best.width = width;
-          best.settle_in = 1;
+          best.settle_in = 3;
           best.algo = BC_ALGO_DELTA;
         }
       }
@@ -1456,6 +1479,23 @@ int bc_autotune(bc_graph_t g, const uint32_t* sources, uint32_t k_probe) {
       if (best_td) best.team_deg = best_td;
     }
   }
+  // the settle test with the settled-neighbour refinement of Delta_node:
+  // fewer, larger batches (high-diameter graphs) against one more gather per
+  // candidate and settle pass (dense graphs)
+  if (best.algo == BC_ALGO_STRICT && !user.settle_in) best.settle_in = 3;
+  if (!user.settle_in && g->dnode2 && best.algo == BC_ALGO_STRICT) {
+    RunCfg r = base;
+    r.team = best.team;
+    r.width = best.width;
+    if (best.warp_deg) r.warp_deg = best.warp_deg;
+    r.team_deg = best.team_deg ? best.team_deg : team_deg_of(r.team, r.warp_deg);
+    r.refine = 1;
+    if (int rc = timed(r, &ms)) return rc;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best.settle_in = 1;
+    }
+  }
   // sources in flight: the full resident capacity, or half of it
   if (!user.max_slots) {
     RunCfg r = base;
@@ -1464,6 +1504,7 @@ int bc_autotune(bc_graph_t g, const uint32_t* sources, uint32_t k_probe) {
     r.algo = best.algo == BC_ALGO_DELTA ? ALGO_DELTA : ALGO_STRICT;
     if (best.warp_deg) r.warp_deg = best.warp_deg;
     r.team_deg = best.team_deg ? best.team_deg : team_deg_of(r.team, r.warp_deg);
+    r.refine = best.settle_in == 1 ? 1u : 0u;
     uint32_t full = 0;
     if (int rc = plan_slots(g, r, k_probe, &full)) return rc;
     r.max_slots = std::max<uint32_t>(1, full / 2);

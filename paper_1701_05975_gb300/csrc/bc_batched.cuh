@@ -55,6 +55,9 @@ __host__ __device__ constexpr int unroll_of() {
   return TEAM >= 1024 ? 6 : UNROLL;
 }
 constexpr int NEAR_REGS = 4;          // near-queue entries per thread kept in registers
+// Teams of up to 512 threads also keep near queues of up to NEAR_MID entries
+// per thread in registers (one gather pass, one team-wide scan).
+constexpr int NEAR_MID = 8;
 #ifndef BCGPU_FAR_LEVELS
 #define BCGPU_FAR_LEVELS 16
 #endif
@@ -113,6 +116,10 @@ template <typename D>
 __device__ __forceinline__ D dmin(D a, D b) {
   return a < b ? a : b;
 }
+template <typename D>
+__device__ __forceinline__ D dmax(D a, D b) {
+  return a < b ? b : a;
+}
 
 // d + Delta_node for the OUT threshold (Eq. 2); a vertex without out-edges
 // (Delta_node = UINT32_MAX, only in directed graphs) cannot lower any
@@ -128,6 +135,7 @@ struct TeamShared {
   uint32_t near_len, far_len, far2_len, S_len, nlev;
   uint32_t pair_len, pair_over;
   int stop;
+  D xs;  // every reached vertex whose distance is below xs is settled (the last threshold)
   // strict schedule: per-section SM cycles and queue entries scanned (kept by
   // the team leader in shared memory, out of every thread's registers)
   unsigned long long cyc_expand, cyc_refill, cyc_settle, cyc_back, near_sc, far_sc;
@@ -792,6 +800,24 @@ __device__ __forceinline__ void push_level_pairs_edges(const uint2* pairs, const
   }
 }
 
+// Delta_node(u) (dn), raised to u's second smallest incident weight when u's
+// lightest neighbour is known to be settled: its distance is below xs, and
+// every reached vertex below xs is settled (xs is the previous phase's
+// threshold).  Every edge from u to a vertex still unsettled then weighs at
+// least the returned bound, so Eq. 2's minimum over d(u) + bound(u) and the
+// IN test with it stay legal (Eq. 4's strict test still keeps every
+// predecessor of a settled vertex in an earlier batch) and settle larger
+// batches.  Undirected graphs only (a.refine).
+template <typename D>
+__device__ __forceinline__ uint32_t edge_bound(const BatchArgs& a, const Slab<D>& sl, uint32_t u, uint32_t dn,
+                                               D xs) {
+  if (a.refine) {
+    const uint32_t nb = __ldg(&a.g.dnode_arg[u]);
+    if (nb != NONE && ldcg(&sl.d[nb]) < xs) return __ldg(&a.g.dnode2[u]);
+  }
+  return dn;
+}
+
 // Team leader: add the cycles since the last mark to a section counter.
 template <typename D, int TEAM>
 __device__ __forceinline__ void lap(TeamShared<D, TEAM>& sh, int t, unsigned long long& section) {
@@ -827,6 +853,7 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
     sh.split2 = sat_add<D>((D)0, far_span(a.width));
     sh.staged = 0;
     sh.cyc_expand = sh.cyc_refill = sh.cyc_settle = sh.cyc_back = sh.near_sc = sh.far_sc = 0;
+    sh.xs = 1;  // weights are >= 1: only the source lies below 1
   }
   team_sync<TEAM>();
   uint32_t f0 = 0, f1 = 1;
@@ -945,8 +972,10 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
     // threshold: Delta' = min(min_near (D + Delta_node), split) <= Delta_i
     const uint32_t nl = sh.near_len;
     const D split = sh.split;
+    const D xs = sh.xs;
     const uint32_t S0 = sh.S_len;
     uint32_t nset = 0, kept = 0;
+    D thr_used = 0;
     bool staged_now = false;
     if (nl <= TEAM * NEAR_REGS) {
       staged_now = stage;
@@ -965,7 +994,7 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
         if (j < nl) {
           uu[r] = ldcg(&sl.nearq[j]);
           dd[r] = ldcg(&sl.d[uu[r]]);
-          dn[r] = (D)__ldg(&a.g.dnode[uu[r]]);
+          dn[r] = (D)edge_bound<D>(a, sl, uu[r], __ldg(&a.g.dnode[uu[r]]), xs);
           dni[r] = a.g.dnode_in ? (D)__ldg(&a.g.dnode_in[uu[r]]) : dn[r];
           out = dmin(out, out_key<D>(dd[r], (uint32_t)dn[r]));
           dm = dmin(dm, dd[r]);
@@ -973,6 +1002,7 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
       }
       team_min2<D, TEAM>(out, dm, sh.red);
       const D thr = dmin(out, split);
+      thr_used = thr;
 #pragma unroll
       for (int r = 0; r < NEAR_REGS; ++r) {
         const uint32_t base = r * TEAM;
@@ -1004,6 +1034,61 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
         nset += stot;
         kept += min((uint32_t)TEAM, nl - base) - stot;
       }
+    } else if (TEAM <= 512 && nl <= TEAM * NEAR_MID) {
+      // a mid-sized near queue: one gather pass into registers, then the
+      // whole settle and compaction behind a single team-wide scan of each
+      // thread's take / keep counts (the order inside a batch and inside the
+      // near queue is free); the IN test's minimum incoming weight is read
+      // only for directed graphs, where it differs from Delta_node
+      if (t == 0) sh.near_sc += nl;
+      uint32_t uu[NEAR_MID], dn[NEAR_MID];
+      D dd[NEAR_MID];
+      D out = INF, dm = INF;
+#pragma unroll
+      for (int r = 0; r < NEAR_MID; ++r) {
+        const uint32_t j = r * TEAM + t;
+        uu[r] = 0;
+        dd[r] = INF;
+        dn[r] = 0;
+        if (j < nl) {
+          uu[r] = ldcg(&sl.nearq[j]);
+          dd[r] = ldcg(&sl.d[uu[r]]);
+          dn[r] = edge_bound<D>(a, sl, uu[r], __ldg(&a.g.dnode[uu[r]]), xs);
+          out = dmin(out, out_key<D>(dd[r], dn[r]));
+          dm = dmin(dm, dd[r]);
+        }
+      }
+      team_min2<D, TEAM>(out, dm, sh.red);
+      const D thr = dmin(out, split);
+      thr_used = thr;
+      uint32_t tmask = 0, ntake = 0, nkeep = 0;
+#pragma unroll
+      for (int r = 0; r < NEAR_MID; ++r) {
+        if (r * TEAM + t < nl) {
+          bool take = dd[r] < thr;
+          if (a.settle_in && !take) {
+            const D dni = a.g.dnode_in ? (D)__ldg(&a.g.dnode_in[uu[r]]) : (D)dn[r];
+            take = dd[r] < (D)(dm + dni);
+          }
+          if (take) {
+            tmask |= 1u << r;
+            ++ntake;
+          } else {
+            ++nkeep;
+          }
+        }
+      }
+      uint32_t sx, kx, stot, ktot;
+      team_excl_scan2<TEAM>(ntake, nkeep, &sx, &kx, &stot, &ktot, sh.scan);
+#pragma unroll
+      for (int r = 0; r < NEAR_MID; ++r) {
+        if (r * TEAM + t < nl) {
+          if ((tmask >> r) & 1u) sl.S[S0 + sx++] = uu[r];
+          else sl.nearq[kx++] = uu[r];
+        }
+      }
+      nset = stot;
+      kept = ktot;
     } else {
       if (t == 0) sh.near_sc += 2ull * nl;
       D out = INF, dm = INF;
@@ -1012,12 +1097,13 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
         if (j < nl) {
           const uint32_t u = ldcg(&sl.nearq[j]);
           const D du = ldcg(&sl.d[u]);
-          out = dmin(out, out_key<D>(du, __ldg(&a.g.dnode[u])));
+          out = dmin(out, out_key<D>(du, edge_bound<D>(a, sl, u, __ldg(&a.g.dnode[u]), xs)));
           dm = dmin(dm, du);
         }
       }
       team_min2<D, TEAM>(out, dm, sh.red);
       const D thr = dmin(out, split);
+      thr_used = thr;
       // settle (strict) and compact the near queue in place
       for (uint32_t base = 0; base < nl; base += TEAM) {
         const uint32_t j = base + t;
@@ -1027,7 +1113,8 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
           const D du = ldcg(&sl.d[u]);
           take = du < thr;
           if (a.settle_in && !take)
-            take = du < (D)(dm + (D)__ldg(a.g.dnode_in ? &a.g.dnode_in[u] : &a.g.dnode[u]));
+            take = du < (D)(dm + (D)(a.g.dnode_in ? __ldg(&a.g.dnode_in[u])
+                                                  : edge_bound<D>(a, sl, u, __ldg(&a.g.dnode[u]), xs)));
         }
         uint32_t stot;
         const uint32_t sx = team_excl_scan<TEAM>(take, &stot, sh.scan);
@@ -1056,6 +1143,10 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
         sl.ends[sh.nlev] = S0 + nset;
         if (phases + refills > a.phase_cap) sh.stop = DEV_ERR_TIMEOUT;
       }
+      // every vertex still unsettled now has d >= thr: the ones left in the
+      // queues failed the test, and a relaxation from a settled u gives at
+      // least d(u) + bound(u) >= thr
+      sh.xs = dmax(sh.xs, thr_used);
     }
     lap(sh, t, sh.cyc_settle);
     team_sync<TEAM>();

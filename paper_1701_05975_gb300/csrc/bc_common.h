@@ -18,6 +18,12 @@ struct GraphDev {
   const uint32_t* adjp;     // [nnz] neighbour | weight << col_bits (graphs where both fit 32 bits)
   uint32_t col_bits;        // bits of the neighbour id in an adjp word
   const uint32_t* dnode;    // [n] Delta_node(v) = min incident (directed: outgoing) weight, UINT32_MAX if none
+  // Undirected graphs (nullptr otherwise): the second smallest incident weight
+  // (UINT32_MAX below two entries) and the neighbour of the smallest one
+  // (UINT32_MAX if none): once that neighbour is settled, every edge from v to
+  // a vertex still unsettled weighs at least dnode2[v].
+  const uint32_t* dnode2;
+  const uint32_t* dnode_arg;
   // Directed graphs only (nullptr otherwise): the in-edge CSR, same entry
   // form as the out-edge one, and the minimum incoming weight per vertex.
   const uint64_t* in_row_ptr;
@@ -102,6 +108,7 @@ struct BatchArgs {
   uint32_t nslots;
   uint64_t width;      // near/far split width
   uint32_t settle_in;  // apply the strict IN criterion too
+  uint32_t refine;     // bound each candidate's edges to unsettled vertices by dnode2 once dnode_arg is settled
   uint64_t phase_cap;  // cap on phases + refills per source
   int* err;            // DEV_* status word
   unsigned long long* stats;  // [STAT_COUNT] or nullptr
@@ -122,8 +129,9 @@ cudaError_t launch_batched_delta(const BatchArgs& a, int dist_bits, int team, in
 cudaError_t batched_occupancy_delta(int dist_bits, int team, int* blocks_per_sm);
 
 // Graph preparation and small helpers (bc_prep.cu).
+// dnode2 / dnode_arg may be nullptr (not computed).
 cudaError_t launch_prep(uint32_t n, uint64_t nnz, const uint64_t* row_ptr, const uint32_t* col, const uint32_t* w,
-                        uint2* adj, uint32_t* dnode, cudaStream_t st);
+                        uint2* adj, uint32_t* dnode, uint32_t* dnode2, uint32_t* dnode_arg, cudaStream_t st);
 // Packed form: adjp[e] = col[e] | w[e] << col_bits (caller checked that both fit).
 cudaError_t launch_pack32(uint64_t nnz, const uint32_t* col, const uint32_t* w, uint32_t col_bits, uint32_t* adjp,
                           cudaStream_t st);

@@ -26,17 +26,46 @@ __global__ void pack32_kernel(uint64_t nnz, const uint32_t* __restrict__ col, co
     adjp[e] = col[e] | (w[e] << col_bits);
 }
 
-__global__ void dnode_kernel(uint32_t n, const uint64_t* __restrict__ row_ptr, const uint32_t* __restrict__ w,
-                             uint32_t* __restrict__ dnode) {
+// One warp per row: the smallest weight (Delta_node), and optionally the
+// second smallest (counting repeats) and the neighbour of the smallest (the
+// lowest id among equal weights).
+__global__ void dnode_kernel(uint32_t n, const uint64_t* __restrict__ row_ptr, const uint32_t* __restrict__ col,
+                             const uint32_t* __restrict__ w, uint32_t* __restrict__ dnode,
+                             uint32_t* __restrict__ dnode2, uint32_t* __restrict__ dnode_arg) {
   const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
   const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   const int lane = threadIdx.x & 31;
   for (uint64_t v = warp; v < n; v += nwarps) {
-    uint32_t m = 0xffffffffu;
-    for (uint64_t e = row_ptr[v] + lane; e < row_ptr[v + 1]; e += 32) m = min(m, w[e]);
+    uint32_t m1 = 0xffffffffu, m2 = 0xffffffffu, a1 = 0xffffffffu;
+    for (uint64_t e = row_ptr[v] + lane; e < row_ptr[v + 1]; e += 32) {
+      const uint32_t x = w[e];
+      const uint32_t c = col[e];
+      if (x < m1 || (x == m1 && c < a1)) {
+        m2 = m1;
+        m1 = x;
+        a1 = c;
+      } else if (x < m2) {
+        m2 = x;
+      }
+    }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0) dnode[v] = m;
+    for (int o = 16; o > 0; o >>= 1) {
+      const uint32_t o1 = __shfl_xor_sync(0xffffffffu, m1, o);
+      const uint32_t o2 = __shfl_xor_sync(0xffffffffu, m2, o);
+      const uint32_t oa = __shfl_xor_sync(0xffffffffu, a1, o);
+      // the two smallest of both lanes' pairs; the smaller first weight keeps its neighbour
+      const uint32_t n2 = min(min(m2, o2), max(m1, o1));
+      if (o1 < m1 || (o1 == m1 && oa < a1)) {
+        m1 = o1;
+        a1 = oa;
+      }
+      m2 = n2;
+    }
+    if (lane == 0) {
+      dnode[v] = m1;
+      if (dnode2) dnode2[v] = m2;
+      if (dnode_arg) dnode_arg[v] = a1;
+    }
   }
 }
 
@@ -74,9 +103,9 @@ int grid_for(uint64_t work, int block) {
 }  // namespace
 
 cudaError_t launch_prep(uint32_t n, uint64_t nnz, const uint64_t* row_ptr, const uint32_t* col, const uint32_t* w,
-                        uint2* adj, uint32_t* dnode, cudaStream_t st) {
+                        uint2* adj, uint32_t* dnode, uint32_t* dnode2, uint32_t* dnode_arg, cudaStream_t st) {
   if (nnz > 0 && adj) pack_adj_kernel<<<grid_for(nnz, 256), 256, 0, st>>>(nnz, col, w, adj);
-  dnode_kernel<<<grid_for((uint64_t)n * 32, 256), 256, 0, st>>>(n, row_ptr, w, dnode);
+  dnode_kernel<<<grid_for((uint64_t)n * 32, 256), 256, 0, st>>>(n, row_ptr, col, w, dnode, dnode2, dnode_arg);
   return cudaGetLastError();
 }
 

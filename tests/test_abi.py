@@ -41,7 +41,7 @@ def test_config_roundtrip_without_gpu(built):
     with pytest.raises(bc.BCError) as ei:
         bc.bc_set_config(team_threads=48)
     assert ei.value.code == bc.BC_ERR_INVALID
-    for bad in (dict(algorithm=3), dict(settle_in=3), dict(mem_fraction=0.99),
+    for bad in (dict(algorithm=3), dict(settle_in=4), dict(mem_fraction=0.99),
                 dict(warp_degree=64, team_degree=32), dict(mode=2)):
         with pytest.raises(bc.BCError):
             bc.bc_set_config(**bad)

@@ -54,7 +54,7 @@ def test_random_graphs_random_configurations(seed):
         g, directed = random_graph(rng)
         cfg = dict(team_threads=int(rng.choice([32, 128, 256, 512, 1024])),
                    bucket_width=int(rng.choice([0, 1, 5, 100, 1 << 30])),
-                   settle_in=int(rng.choice([1, 2])),
+                   settle_in=int(rng.choice([1, 2, 3])),
                    algorithm=int(rng.choice([1, 1, 2])),
                    max_slots=int(rng.choice([0, 0, 1, 7])))
         bc.bc_set_config(**cfg)
