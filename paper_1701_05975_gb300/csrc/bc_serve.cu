@@ -11,7 +11,7 @@
 // their graphs, onto up to 8 streams, so batches of different requests
 // overlap on the device and a request's batches interleave with other
 // requests' batches.  Before each batch it re-divides the GPU's resident
-// threads: a request's share is capacity / min(requests with work left, 4),
+// threads: a request's share is capacity / min(requests with work left, 2),
 // so a large request takes the whole GPU while it runs alone and gives way
 // at its next batch boundary when others arrive.  Among requests waiting for
 // their next batch, the earliest deadline goes first: submit time + its work
@@ -74,7 +74,7 @@ struct Request {
 #define BCGPU_SERVE_STREAMS 8
 #endif
 #ifndef BCGPU_SERVE_SHARE
-#define BCGPU_SERVE_SHARE 4
+#define BCGPU_SERVE_SHARE 2
 #endif
 #ifndef BCGPU_SERVE_WAVES
 #define BCGPU_SERVE_WAVES 2
