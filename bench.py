@@ -765,13 +765,17 @@ def main():
     G.close()
     if ws == 1 and not args.no_serving and args.workload == "rmat20":
         # the serving half of the metric (p50/p99 latency, aggregate GTEPS),
-        # measured after the batched workload's graph and workspaces are freed
-        sv = serving_measure(args)
-        line["serving"] = {"workload": WORKLOADS["serving"][0], "gteps": sv["gteps"], "unit": "GTEPS",
-                           "latency_ms": sv["latency_ms"], "requests": sv["requests"], "load": sv["load"],
-                           "arrival_rate_per_s": sv["arrival_rate_per_s"],
-                           "saturated_rate_per_s": sv["saturated_rate_per_s"], "completed": sv["completed"],
-                           "failed": sv["failed"], "max_concurrent": sv["max_concurrent"]}
+        # measured after the batched workload's graph and workspaces are freed;
+        # a failure there is reported in the line instead of losing the line
+        try:
+            sv = serving_measure(args)
+            line["serving"] = {"workload": WORKLOADS["serving"][0], "gteps": sv["gteps"], "unit": "GTEPS",
+                               "latency_ms": sv["latency_ms"], "requests": sv["requests"], "load": sv["load"],
+                               "arrival_rate_per_s": sv["arrival_rate_per_s"],
+                               "saturated_rate_per_s": sv["saturated_rate_per_s"], "completed": sv["completed"],
+                               "failed": sv["failed"], "max_concurrent": sv["max_concurrent"]}
+        except Exception as exc:  # noqa: BLE001 - any failure of the serving half is reported as such
+            line["serving"] = {"workload": WORKLOADS["serving"][0], "error": f"{type(exc).__name__}: {exc}"}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g, sources, opts)
     emit(line, rank)

@@ -227,11 +227,12 @@ int bc_compute_paper_variant(bc_graph_t g, const uint32_t *sources, uint32_t k, 
  * sources in flight as the GPU holds for its graph).  Every admitted request
  * runs as a sequence of source batches (about two waves of its sources in
  * flight each); a scheduler thread interleaves the batches of all admitted
- * requests on up to 8 streams, least remaining work first, and re-divides the
- * GPU's resident threads at every batch among the requests with work left
- * (at most 4 ways), so batches of different graphs run on the device at the
- * same time and a large request yields at its batch boundaries.  Not in the
- * paper: a serving layer around its per-source method.
+ * requests on up to 8 streams, earliest deadline first (submit time + the
+ * request's entries to walk / the measured aggregate rate), and re-divides
+ * the GPU's resident threads at every batch among the requests with work
+ * left (at most 2 ways), so batches of different graphs run on the device at
+ * the same time and a large request yields at its batch boundaries.  Not in
+ * the paper: a serving layer around its per-source method.
  * BC_ERR_NOMEM: the request alone can never fit the memory budget.
  * BC_ERR_BUSY: the pending queue is full.
  */

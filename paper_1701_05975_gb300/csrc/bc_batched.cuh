@@ -141,11 +141,6 @@ struct TeamShared {
   unsigned long long cyc_expand, cyc_refill, cyc_settle, cyc_back, near_sc, far_sc;
   long long tmark;
   D split, split2;  // near < split <= far < split2 <= far2
-  // at most the smallest distance of a live far entry: every decrease that
-  // lands in [split, split2) lowers it, each refill resets it to the exact
-  // minimum of the entries it keeps
-  D fmin;
-  D kmin;  // the refill in progress: smallest distance among the far entries it keeps
   uint32_t off[TEAM + 1];
   uint32_t vtx[TEAM];
   unsigned long long rs[TEAM];
@@ -532,7 +527,6 @@ __device__ __forceinline__ void visit_entry(const Slab<D>& sl, TeamShared<D, TEA
         } else {
           const D split2 = sh.split2;
           if (nd < split2) {
-            atomic_min_d(&sh.fmin, nd);
             if (old >= split2) sl.farq[atomicAdd(&sh.far_len, 1u)] = u;
           } else if (old == INF) {
             sl.farq2[atomicAdd(&sh.far2_len, 1u)] = u;
@@ -850,8 +844,6 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
     sh.near_len = 0;
     sh.far_len = 0;
     sh.far2_len = 0;
-    sh.fmin = INF;
-    sh.kmin = INF;
     sh.S_len = 1;
     sh.nlev = 1;
     sh.pair_len = 0;
@@ -910,12 +902,8 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
             u = ldcg(&sl.farq2[j]);
             const D du = ldcg(&sl.d[u]);
             if (du >= old2) {  // below old2: queued again in a lower range already
-              if (du < ns2) {
-                sl.farq[atomicAdd(&sh.far_len, 1u)] = u;
-                atomic_min_d(&sh.fmin, du);
-              } else {
-                keep = 1;
-              }
+              if (du < ns2) sl.farq[atomicAdd(&sh.far_len, 1u)] = u;
+              else keep = 1;
             }
           }
           uint32_t ktot;
@@ -937,13 +925,17 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
       const D old = sh.split;
       const D cap = sh.split2;
       const uint32_t fl = sh.far_len;
-      if (t == 0) sh.far_sc += fl;
-      // the new split from the tracked minimum (no pass over the queue); a
-      // stale contribution (a vertex that has since dropped below the split)
-      // only makes it smaller: a smaller split is legal, and a refill that
-      // moves nothing resets the minimum to the exact one below
-      const D lo = sh.fmin;
-      const D ns = (lo == INF) ? old : dmin(sat_add<D>(lo < old ? old : lo, a.width), cap);
+      if (t == 0) sh.far_sc += 2ull * fl;
+      D lo = INF, dummy = INF;
+      for (uint32_t base = 0; base < fl; base += TEAM) {
+        const uint32_t j = base + t;
+        if (j < fl) {
+          const D du = ldcg(&sl.d[ldcg(&sl.farq[j])]);
+          if (du >= old) lo = dmin(lo, du);
+        }
+      }
+      team_min2<D, TEAM>(lo, dummy, sh.red);
+      const D ns = (lo == INF) ? old : dmin(sat_add<D>(lo, a.width), cap);
       uint32_t kept = 0;
       for (uint32_t base = 0; base < fl; base += TEAM) {
         const uint32_t j = base + t;
@@ -956,7 +948,6 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
               sl.nearq[atomicAdd(&sh.near_len, 1u)] = u;
             } else {
               keep = 1;
-              atomic_min_d(&sh.kmin, du);
             }
           }
         }
@@ -970,8 +961,6 @@ __device__ bool run_source(const BatchArgs& a, const Slab<D>& sl, TeamShared<D, 
       if (t == 0) {
         sh.far_len = kept;
         sh.split = ns;
-        sh.fmin = sh.kmin;  // exact for the next refill, until decreases lower it
-        sh.kmin = INF;
       }
       ++refills;
       if (phases + refills > a.phase_cap && t == 0) sh.stop = DEV_ERR_TIMEOUT;
