@@ -128,6 +128,49 @@ def test_complete_graph_zero(n):
     assert np.all(oracle.bc(g, np.arange(n), 0.5) == 0)
 
 
+def undirected_edge_sums(g, ebc):
+    """Edge BC per undirected edge {a, b}: the sum of its two CSR entries."""
+    rows, cols, _ = g.edges()
+    und = {}
+    for e, (a, b) in enumerate(zip(rows.tolist(), cols.tolist())):
+        key = (min(a, b), max(a, b))
+        und[key] = und.get(key, 0.0) + float(ebc[e])
+    return und
+
+
+@pytest.mark.parametrize("n", [2, 3, 6, 11])
+def test_edge_bc_path_closed_form(n):
+    # edge {i, i+1} of a path lies on the one path of every pair s <= i < t:
+    # (i + 1)(n - 1 - i) unordered pairs, whatever the weights
+    rng = np.random.default_rng(100 + n)
+    g = graph(n, [(i, i + 1, int(rng.integers(1, 40))) for i in range(n - 1)])
+    und = undirected_edge_sums(g, oracle.edge_bc(g, np.arange(n), 0.5))
+    assert und == {(i, i + 1): float((i + 1) * (n - 1 - i)) for i in range(n - 1)}
+
+
+@pytest.mark.parametrize("n", [2, 4, 9])
+def test_edge_bc_star_closed_form(n):
+    # the spoke to a leaf carries exactly the n - 1 pairs that contain the leaf
+    rng = np.random.default_rng(200 + n)
+    g = graph(n, [(0, i, int(rng.integers(1, 9))) for i in range(1, n)])
+    und = undirected_edge_sums(g, oracle.edge_bc(g, np.arange(n), 0.5))
+    assert und == {(0, i): float(n - 1) for i in range(1, n)}
+
+
+@pytest.mark.parametrize("n", [3, 4, 5, 8, 9])
+def test_edge_bc_unit_cycle_closed_form(n):
+    # by symmetry every edge carries the same share of the pairs' hop counts:
+    # odd n, n pairs at each distance k <= (n-1)/2, one path each:
+    #   n (n-1)(n+1)/8 hops over n edges -> (n^2 - 1)/8 per edge;
+    # even n, the n/2 antipodal pairs split over two n/2-hop paths:
+    #   n^3/8 hops over n edges -> n^2/8 per edge
+    g = graph(n, [(i, (i + 1) % n, 1) for i in range(n)])
+    und = undirected_edge_sums(g, oracle.edge_bc(g, np.arange(n), 0.5))
+    want = (n * n - 1) / 8 if n % 2 else n * n / 8
+    assert len(und) == n
+    np.testing.assert_allclose(list(und.values()), want, rtol=1e-13)
+
+
 def test_unit_grid_binomial_counts():
     a, b = 9, 12
     edges = [(r * b + c, r * b + c + 1, 1) for r in range(a) for c in range(b - 1)]
