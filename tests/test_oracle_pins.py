@@ -353,6 +353,50 @@ def test_fig1a_strict_vs_nonstrict():
     assert np.array_equal(d_ns, d_b)
 
 
+def test_phased_unit_weights_settle_bfs_layers():
+    # with every weight 1, Delta_node = 1, so Eq. 2 gives Delta_i = min_U d + 1
+    # and Eq. 4 settles exactly the candidates at the smallest distance: the
+    # batches are the breadth-first layers (level = hop distance from s)
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import shortest_path
+
+    rng = np.random.default_rng(31)
+    graphs = [gen.er_graph(150, 260, 1, 1, seed=32), gen.grid_graph(7, 9, wmin=1, wmax=1, seed=33),
+              graph(12, [(i, i + 1, 1) for i in range(11)])]
+    for g in graphs:
+        rows, cols, _ = g.edges()
+        mat = sp.csr_matrix((np.ones(len(rows)), (rows, cols)), shape=(g.n, g.n))
+        for s in rng.choice(g.n, size=4, replace=False):
+            hops = shortest_path(mat, unweighted=True, indices=int(s))
+            _, _, lev, _, nlev = oracle.phased(g, int(s))
+            reach = np.isfinite(hops)
+            assert np.array_equal(lev[reach], hops[reach].astype(np.uint32))
+            assert np.all(lev[~reach] == np.iinfo(np.uint32).max)
+            assert nlev == int(hops[reach].max()) + 1
+
+
+def test_phased_weighted_star_batches():
+    # from the centre every leaf is a candidate with d = w and Delta_node = w,
+    # so each batch takes every remaining leaf lighter than twice the lightest
+    rng = np.random.default_rng(41)
+    for trial in range(20):
+        n = int(rng.integers(3, 14))
+        ws = [int(x) for x in rng.integers(1, 30, size=n - 1)]
+        g = graph(n, [(0, i + 1, ws[i]) for i in range(n - 1)])
+        want = {0: 0}
+        left, level = set(range(1, n)), 1
+        while left:
+            lightest = min(ws[v - 1] for v in left)
+            batch = {v for v in left if ws[v - 1] < 2 * lightest}
+            for v in batch:
+                want[v] = level
+            left -= batch
+            level += 1
+        _, _, lev, _, nlev = oracle.phased(g, 0)
+        assert [int(x) for x in lev] == [want[v] for v in range(n)], (ws, lev)
+        assert nlev == level
+
+
 def test_phased_strict_matches_brandes_and_levels_are_legal():
     rng = np.random.default_rng(21)
     graphs = list(small_graphs(60, seed=22, wmax=4)) + [gen.er_graph(200, 700, 1, 6, seed=23),
